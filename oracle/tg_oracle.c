@@ -1,0 +1,491 @@
+/*
+ * TaylorGrid oracle: a plain, slow, obviously-correct FP64 CPU statement of the
+ * TaylorGrid method (arXiv 2402.14415), written from the paper.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or load
+ * this file; only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it. It shares no code, header, table or constant generator with
+ * the CUDA library.
+ *
+ * Conventions (readings of points the paper leaves open):
+ *  - Domain [0,1]^D, `res` vertices per axis, vertex j at x = j/(res-1).
+ *  - Offsets x - v_i (Eq. 3) are measured in grid units, delta = t - b_i in [-1,1]^D.
+ *  - Corner i has offset bits b_d = (i >> d) & 1 (x fastest).
+ *  - Coefficients per vertex and channel, in this order:
+ *      3-D: f, g_x, g_y, g_z, H_xx, H_yy, H_zz, H_xy, H_xz, H_yz   (K = 1 / 4 / 10)
+ *      2-D: f, g_x, g_y, H_xx, H_yy, H_xy                           (K = 1 / 3 / 6)
+ *    H holds the true Hessian entries; the symmetric H is assembled and the
+ *    quadratic form of Eq. 1 evaluated as written.
+ *  - Exchange layout of a grid: [vertex][channel][k], vertex = x + res*(y + res*z).
+ *  - Index rule (Eq. 2, `query`): clamp x to [0,1]; u = fl32(x * (res-1));
+ *    c = min(floor(u), res-2); t = fl32(u - c). The oracle runs exactly these
+ *    FP32 operations and only then promotes t to FP64.
+ *
+ * Parity pins live in tests/test_oracle_pins.py. Functions without an
+ * independent pin say "parity unpinned" in their comment.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TGO_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------ */
+/* Sizes                                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Number of Taylor coefficients of a truncated series of order `order` in D
+ * variables: C(D + order, order) (the value, D first derivatives and the
+ * D(D+1)/2 distinct second derivatives; Sec. 3.1, Eq. 1). */
+TGO_API int tgo_num_coefs(int dim, int order)
+{
+    int k = 1;
+    if (order >= 1) k += dim;
+    if (order >= 2) k += dim * (dim + 1) / 2;
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 2: query(x, V_T) -> the Taylor voxel that contains x                  */
+/* ------------------------------------------------------------------------ */
+TGO_API void tgo_locate(int dim, int res, const float *x, int *cell, double *t)
+{
+    for (int d = 0; d < dim; ++d) {
+        float xd = x[d];
+        xd = fmaxf(xd, 0.0f);             /* NaN -> 0 (fmax drops the NaN) */
+        xd = fminf(xd, 1.0f);
+        volatile float scale = (float)(res - 1);
+        volatile float u = xd * scale;    /* one FP32 multiply, no contraction */
+        int c = (int)floorf(u);
+        if (c > res - 2) c = res - 2;
+        if (c < 0) c = 0;
+        volatile float tf = u - (float)c; /* FP32 subtraction */
+        cell[d] = c;
+        t[d] = (double)tf;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 / Eq. 3: the truncated series T'(delta; S(v)) of one vertex        */
+/* ------------------------------------------------------------------------ */
+
+/* Unpack the stored coefficients into f, the gradient g and the full
+ * symmetric Hessian H (zero where the order does not reach). */
+static void unpack(int dim, int order, const double *th, double *f, double g[3], double H[3][3])
+{
+    *f = th[0];
+    for (int a = 0; a < 3; ++a) { g[a] = 0; for (int b = 0; b < 3; ++b) H[a][b] = 0; }
+    if (order >= 1) for (int a = 0; a < dim; ++a) g[a] = th[1 + a];
+    if (order >= 2) {
+        const double *h = th + 1 + dim;
+        for (int a = 0; a < dim; ++a) H[a][a] = h[a];
+        if (dim == 3) {
+            H[0][1] = H[1][0] = h[3];
+            H[0][2] = H[2][0] = h[4];
+            H[1][2] = H[2][1] = h[5];
+        } else {
+            H[0][1] = H[1][0] = h[2];
+        }
+    }
+}
+
+/* T = f + g^T delta + 1/2 delta^T H delta  (Eq. 1 truncated at the order). */
+static double series_value(int dim, int order, const double *th, const double *delta)
+{
+    double f, g[3], H[3][3];
+    unpack(dim, order, th, &f, g, H);
+    double lin = 0, quad = 0;
+    for (int a = 0; a < dim; ++a) lin += g[a] * delta[a];
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) quad += delta[a] * H[a][b] * delta[b];
+    return f + lin + 0.5 * quad;
+}
+
+/* d T / d delta = g + H delta. */
+static void series_gradient(int dim, int order, const double *th, const double *delta, double *out)
+{
+    double f, g[3], H[3][3];
+    unpack(dim, order, th, &f, g, H);
+    for (int a = 0; a < dim; ++a) {
+        double s = g[a];
+        for (int b = 0; b < dim; ++b) s += H[a][b] * delta[b];
+        out[a] = s;
+    }
+}
+
+/* dT/dtheta_k at delta, i.e. T with the unit coefficient vector e_k
+ * (T is linear in its coefficients). */
+static void series_jacobian(int dim, int order, const double *delta, double *phi)
+{
+    int K = tgo_num_coefs(dim, order);
+    double e[10];
+    for (int k = 0; k < K; ++k) {
+        memset(e, 0, sizeof e);
+        e[k] = 1.0;
+        phi[k] = series_value(dim, order, e, delta);
+    }
+}
+
+/* d/d delta_a of dT/dtheta_k. */
+static void series_jacobian_grad(int dim, int order, const double *delta, double dphi[][3])
+{
+    int K = tgo_num_coefs(dim, order);
+    double e[10], gr[3];
+    for (int k = 0; k < K; ++k) {
+        memset(e, 0, sizeof e);
+        e[k] = 1.0;
+        series_gradient(dim, order, e, delta, gr);
+        for (int a = 0; a < 3; ++a) dphi[k][a] = a < dim ? gr[a] : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 4: interp(x, v_L), the multilinear blend of the 2^D corner values     */
+/* ------------------------------------------------------------------------ */
+static double corner_weight(int dim, int i, const double *t)
+{
+    double w = 1.0;
+    for (int d = 0; d < dim; ++d) w *= ((i >> d) & 1) ? t[d] : 1.0 - t[d];
+    return w;
+}
+
+static double corner_weight_grad(int dim, int i, const double *t, int a)
+{
+    double w = 1.0;
+    for (int d = 0; d < dim; ++d) {
+        int b = (i >> d) & 1;
+        if (d == a) w *= b ? 1.0 : -1.0;
+        else w *= b ? t[d] : 1.0 - t[d];
+    }
+    return w;
+}
+
+static int64_t vertex_index(int dim, int res, const int *cell, int i)
+{
+    int64_t v = 0, stride = 1;
+    for (int d = 0; d < dim; ++d) { v += (int64_t)(cell[d] + ((i >> d) & 1)) * stride; stride *= res; }
+    return v;
+}
+
+/* Field value and spatial gradient (grid units) of every channel for a
+ * given cell and local coordinate t (Eq. 3 + Eq. 4). */
+TGO_API void tgo_eval_cell(int dim, int res, int order, int C, const double *coefs,
+                           const int *cell, const double *t, double *f_out, double *gu_out)
+{
+    int K = tgo_num_coefs(dim, order);
+    for (int ch = 0; ch < C; ++ch) {
+        double f = 0, gu[3] = {0, 0, 0};
+        for (int i = 0; i < (1 << dim); ++i) {
+            double delta[3] = {0, 0, 0}, dT[3];
+            for (int d = 0; d < dim; ++d) delta[d] = t[d] - (double)((i >> d) & 1);
+            const double *th = coefs + (vertex_index(dim, res, cell, i) * C + ch) * K;
+            double Ti = series_value(dim, order, th, delta);   /* Eq. 3 */
+            series_gradient(dim, order, th, delta, dT);
+            double w = corner_weight(dim, i, t);
+            f += w * Ti;                                        /* Eq. 4 */
+            for (int a = 0; a < dim; ++a) gu[a] += corner_weight_grad(dim, i, t, a) * Ti + w * dT[a];
+        }
+        f_out[ch] = f;
+        if (gu_out) for (int a = 0; a < dim; ++a) gu_out[ch * dim + a] = gu[a];
+    }
+}
+
+/* Forward query of N points: values (N x C), optional world-unit spatial
+ * gradients (N x C x D), optional cells (N x D) and local coordinates. */
+TGO_API void tgo_query(int dim, int res, int order, int C, const double *coefs, int64_t N,
+                       const float *pts, double *out, double *grad_x, int32_t *cells, double *ts)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        int cell[3]; double t[3], gu[16 * 3];
+        tgo_locate(dim, res, pts + n * dim, cell, t);
+        tgo_eval_cell(dim, res, order, C, coefs, cell, t, out + n * C, gu);
+        if (grad_x) for (int j = 0; j < C * dim; ++j) grad_x[n * C * dim + j] = gu[j] * (double)(res - 1);
+        if (cells) for (int d = 0; d < dim; ++d) cells[n * dim + d] = cell[d];
+        if (ts) for (int d = 0; d < dim; ++d) ts[n * dim + d] = t[d];
+    }
+}
+
+/* Coefficient gradient (direct grid optimisation, Sec. 3.1 / Sec. 3.3):
+ * the field is linear in the coefficients, so dL/dtheta = J^T dL/df with
+ * J_{n,(i,k)} = w_i(t) phi_k(delta_i), plus the same for the spatial gradient
+ * with d/du of (w_i phi_k). Accumulates into coef_grad; abs_grad (optional)
+ * accumulates |contribution| for the scale-aware tolerance. */
+TGO_API void tgo_query_backward(int dim, int res, int order, int C, int64_t N, const float *pts,
+                                const double *dL_df, const double *dL_dgx,
+                                double *coef_grad, double *abs_grad)
+{
+    int K = tgo_num_coefs(dim, order);
+    double hinv = (double)(res - 1);
+    #pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        int cell[3]; double t[3];
+        tgo_locate(dim, res, pts + n * dim, cell, t);
+        for (int i = 0; i < (1 << dim); ++i) {
+            double delta[3] = {0, 0, 0}, phi[10], dphi[10][3];
+            for (int d = 0; d < dim; ++d) delta[d] = t[d] - (double)((i >> d) & 1);
+            series_jacobian(dim, order, delta, phi);
+            series_jacobian_grad(dim, order, delta, dphi);
+            double w = corner_weight(dim, i, t), dw[3];
+            for (int a = 0; a < dim; ++a) dw[a] = corner_weight_grad(dim, i, t, a);
+            int64_t v = vertex_index(dim, res, cell, i);
+            for (int ch = 0; ch < C; ++ch) {
+                for (int k = 0; k < K; ++k) {
+                    double c = w * phi[k] * dL_df[n * C + ch];
+                    if (dL_dgx)
+                        for (int a = 0; a < dim; ++a)
+                            c += hinv * dL_dgx[(n * C + ch) * dim + a] * (dw[a] * phi[k] + w * dphi[k][a]);
+                    int64_t j = (v * C + ch) * K + k;
+                    #pragma omp atomic
+                    coef_grad[j] += c;
+                    if (abs_grad) {
+                        double a = fabs(c);
+                        #pragma omp atomic
+                        abs_grad[j] += a;
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* Per-point scale of the forward value for the tolerance: sum_i w_i sum_k |theta phi_k|. */
+TGO_API void tgo_query_absscale(int dim, int res, int order, int C, const double *coefs, int64_t N,
+                                const float *pts, double *scale)
+{
+    int K = tgo_num_coefs(dim, order);
+    #pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        int cell[3]; double t[3];
+        tgo_locate(dim, res, pts + n * dim, cell, t);
+        for (int ch = 0; ch < C; ++ch) {
+            double s = 0;
+            for (int i = 0; i < (1 << dim); ++i) {
+                double delta[3] = {0, 0, 0}, phi[10];
+                for (int d = 0; d < dim; ++d) delta[d] = t[d] - (double)((i >> d) & 1);
+                series_jacobian(dim, order, delta, phi);
+                const double *th = coefs + (vertex_index(dim, res, cell, i) * C + ch) * K;
+                double w = corner_weight(dim, i, t);
+                for (int k = 0; k < K; ++k) s += w * fabs(th[k] * phi[k]);
+            }
+            scale[n * C + ch] = s;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Optimiser. The paper fixes only the learning rate (Sec. 4.1); the build   */
+/* uses Adam (Kingma & Ba 2015, Algorithm 1) with bias correction, step >= 1. */
+/* ------------------------------------------------------------------------ */
+TGO_API void tgo_adam(int64_t n, double *p, double *g, double *m, double *v,
+                      double lr, double beta1, double beta2, double eps, int64_t step)
+{
+    double bc1 = 1.0 - pow(beta1, (double)step);
+    double bc2 = 1.0 - pow(beta2, (double)step);
+    for (int64_t j = 0; j < n; ++j) {
+        m[j] = beta1 * m[j] + (1.0 - beta1) * g[j];
+        v[j] = beta2 * v[j] + (1.0 - beta2) * g[j] * g[j];
+        double mhat = m[j] / bc1;
+        double vhat = v[j] / bc2;
+        p[j] -= lr * mhat / (sqrt(vhat) + eps);
+        g[j] = 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* SDF targets (Sec. 3.2, Eq. 5): analytic signed distances                  */
+/* ------------------------------------------------------------------------ */
+
+/* sphere (cx,cy,cz,r): |x - c| - r;  box (cx,cy,cz,hx,hy,hz): distance to the
+ * box surface, negative inside; the union is the minimum of the members. */
+TGO_API double tgo_sdf_union(int ns, const float *sph, int nb, const float *box, const double *x)
+{
+    double best = INFINITY;
+    for (int s = 0; s < ns; ++s) {
+        const float *q = sph + 4 * s;
+        double dx = x[0] - q[0], dy = x[1] - q[1], dz = x[2] - q[2];
+        double d = sqrt(dx * dx + dy * dy + dz * dz) - q[3];
+        if (d < best) best = d;
+    }
+    for (int b = 0; b < nb; ++b) {
+        const float *q = box + 6 * b;
+        double e[3], outside = 0, inside = -INFINITY;
+        for (int a = 0; a < 3; ++a) {
+            e[a] = fabs(x[a] - q[a]) - q[3 + a];
+            if (e[a] > 0) outside += e[a] * e[a];
+            if (e[a] > inside) inside = e[a];
+        }
+        double d = sqrt(outside) + (inside < 0 ? inside : 0.0);
+        if (d < best) best = d;
+    }
+    return best;
+}
+
+/* One SDF fitting step on given points (Sec. 3.2):
+ *   L = mean_P |f(x) - d(x)|                        (Eq. 6 with w = 1)
+ *     + lambda_eik * mean_P (||grad_x f(x)|| - 1)^2  (IGR eikonal term, Eq. 8)
+ * with d evaluated at the clamped point. The gradient of L with respect to
+ * the coefficients is accumulated into coef_grad. loss[0] = L1 term,
+ * loss[1] = eikonal mean (unweighted), loss[2] = mean |f - d| (same as loss[0]).
+ * sign(0) = 0; a zero spatial gradient (norm < 1e-12) gets zero eikonal grad. */
+TGO_API void tgo_sdf_step(int res, int order, const double *coefs, int64_t N, const float *pts,
+                          int ns, const float *sph, int nb, const float *box,
+                          double lambda_eik, double *coef_grad, double *loss)
+{
+    const int dim = 3;
+    double *f = (double *)malloc(sizeof(double) * N);
+    double *gx = (double *)malloc(sizeof(double) * N * 3);
+    double *dLdf = (double *)malloc(sizeof(double) * N);
+    double *dLdg = (double *)malloc(sizeof(double) * N * 3);
+    tgo_query(dim, res, order, 1, coefs, N, pts, f, gx, NULL, NULL);
+    double l1 = 0, eik = 0;
+    for (int64_t n = 0; n < N; ++n) {
+        double x[3];
+        for (int a = 0; a < 3; ++a) x[a] = fmin(fmax((double)pts[n * 3 + a], 0.0), 1.0);
+        double d = tgo_sdf_union(ns, sph, nb, box, x);
+        double r = f[n] - d;
+        l1 += fabs(r);
+        dLdf[n] = (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (double)N;
+        double nrm = sqrt(gx[3 * n] * gx[3 * n] + gx[3 * n + 1] * gx[3 * n + 1] + gx[3 * n + 2] * gx[3 * n + 2]);
+        eik += (nrm - 1.0) * (nrm - 1.0);
+        for (int a = 0; a < 3; ++a)
+            dLdg[3 * n + a] = nrm < 1e-12 ? 0.0 : lambda_eik * 2.0 * (nrm - 1.0) * gx[3 * n + a] / nrm / (double)N;
+    }
+    tgo_query_backward(dim, res, order, 1, N, pts, dLdf, lambda_eik != 0.0 ? dLdg : NULL, coef_grad, NULL);
+    if (loss) { loss[0] = l1 / (double)N; loss[1] = eik / (double)N; loss[2] = l1 / (double)N; }
+    free(f); free(gx); free(dLdf); free(dLdg);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based generator (splitmix64, Steele/Lea/Flood 2014)               */
+/* ------------------------------------------------------------------------ */
+static uint64_t mix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+TGO_API double tgo_uniform(uint64_t seed, uint64_t stream, uint64_t idx)
+{
+    uint64_t k = mix64(mix64(mix64(seed) + stream) + idx);
+    return (double)(k >> 40) * (1.0 / 16777216.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Volume rendering (Sec. 3.3, Eq. 9 - Eq. 11)                                */
+/* ------------------------------------------------------------------------ */
+static double softplus(double x) { return x > 30.0 ? x : log1p(exp(x)); }
+static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+/* Ray / unit-cube slab intersection. Returns 1 and [near, far] on a hit. */
+TGO_API int tgo_ray_box(const double *o, const double *d, double *near_, double *far_)
+{
+    double tn = 0.0, tf = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (o[a] < 0.0 || o[a] > 1.0) return 0;
+            continue;
+        }
+        double t0 = (0.0 - o[a]) / d[a], t1 = (1.0 - o[a]) / d[a];
+        if (t0 > t1) { double s = t0; t0 = t1; t1 = s; }
+        if (t0 > tn) tn = t0;
+        if (t1 < tf) tf = t1;
+    }
+    if (!(tf > tn)) return 0;
+    *near_ = tn; *far_ = tf;
+    return 1;
+}
+
+/* Render R rays through a density grid (order od, 1 channel, sigma =
+ * softplus(f), Eq. 9) and a colour grid (order oc, 3 channels, c =
+ * sigmoid(f)), both res^3, with S stratified samples per ray:
+ *   t_i = near + (i + xi_i) (far - near) / S, xi_i = U(seed, ray_base + r, i),
+ *   delta_i = t_{i+1} - t_i (t_S = far),
+ *   C = sum_i T_i (1 - exp(-sigma_i delta_i)) c_i + T_S * bg           (Eq. 10)
+ * A ray that misses the cube renders bg. If `target` is given, the loss
+ * (1/R) sum_r ||C_r - target_r||^2 (Eq. 11) is returned in *loss and its
+ * gradient is accumulated into dgrad / cgrad (coefficient gradients of the
+ * two grids). The per-sample derivatives are taken term by term from Eq. 10:
+ *   dC/dc_i     = T_i alpha_i
+ *   dC/dsigma_i = delta_i T_{i+1} c_i - delta_i (sum_{j>i} T_j alpha_j c_j + T_S bg)
+ */
+TGO_API void tgo_render(int res, int od, const double *dcoef, int oc, const double *ccoef,
+                        int64_t R, int S, const float *rays_o, const float *rays_d,
+                        uint64_t seed, uint64_t ray_base, double bg, double *rgb_out,
+                        const float *target, double *dgrad, double *cgrad, double *loss)
+{
+    double total = 0.0;
+    double *sig = (double *)malloc(sizeof(double) * S);
+    double *fs = (double *)malloc(sizeof(double) * S);
+    double *col = (double *)malloc(sizeof(double) * S * 3);
+    double *del = (double *)malloc(sizeof(double) * S);
+    double *Tr = (double *)malloc(sizeof(double) * (S + 1));
+    float *xs = (float *)malloc(sizeof(float) * S * 3);
+    for (int64_t r = 0; r < R; ++r) {
+        double o[3], d[3], nr, fr;
+        for (int a = 0; a < 3; ++a) { o[a] = rays_o[3 * r + a]; d[a] = rays_d[3 * r + a]; }
+        double C[3] = {bg, bg, bg};
+        int hit = tgo_ray_box(o, d, &nr, &fr);
+        if (hit) {
+            double ts_next = 0;
+            for (int i = 0; i < S; ++i) {
+                double xi = tgo_uniform(seed, ray_base + (uint64_t)r, (uint64_t)i);
+                double ti = nr + ((double)i + xi) * (fr - nr) / (double)S;
+                double xi1 = i + 1 < S ? tgo_uniform(seed, ray_base + (uint64_t)r, (uint64_t)(i + 1)) : 0;
+                ts_next = i + 1 < S ? nr + ((double)(i + 1) + xi1) * (fr - nr) / (double)S : fr;
+                del[i] = ts_next - ti;
+                for (int a = 0; a < 3; ++a) xs[3 * i + a] = (float)(o[a] + ti * d[a]);
+            }
+            double fc[3];
+            for (int i = 0; i < S; ++i) {
+                double fd;
+                int cell[3]; double t[3];
+                tgo_locate(3, res, xs + 3 * i, cell, t);
+                tgo_eval_cell(3, res, od, 1, dcoef, cell, t, &fd, NULL);
+                tgo_eval_cell(3, res, oc, 3, ccoef, cell, t, fc, NULL);
+                fs[i] = fd;
+                sig[i] = softplus(fd);
+                for (int a = 0; a < 3; ++a) col[3 * i + a] = sigmoid(fc[a]);
+            }
+            /* Eq. 10: T_i = exp(-sum_{j<i} sigma_j delta_j) */
+            for (int i = 0; i <= S; ++i) {
+                double acc = 0;
+                for (int j = 0; j < i; ++j) acc += sig[j] * del[j];
+                Tr[i] = exp(-acc);
+            }
+            for (int a = 0; a < 3; ++a) {
+                double c = 0;
+                for (int i = 0; i < S; ++i) c += Tr[i] * (1.0 - exp(-sig[i] * del[i])) * col[3 * i + a];
+                C[a] = c + Tr[S] * bg;
+            }
+            if (target) {
+                double g[3];
+                for (int a = 0; a < 3; ++a) g[a] = 2.0 * (C[a] - (double)target[3 * r + a]) / (double)R;
+                for (int i = 0; i < S; ++i) {
+                    double alpha = 1.0 - exp(-sig[i] * del[i]);
+                    double dsig = 0, dcol[3];
+                    for (int a = 0; a < 3; ++a) {
+                        double rest = Tr[S] * bg;
+                        for (int j = i + 1; j < S; ++j) rest += Tr[j] * (1.0 - exp(-sig[j] * del[j])) * col[3 * j + a];
+                        dsig += g[a] * (del[i] * Tr[i + 1] * col[3 * i + a] - del[i] * rest);
+                        dcol[a] = g[a] * Tr[i] * alpha;
+                    }
+                    /* chain through sigma = softplus(f) and c = sigmoid(f) into Eq. 3/4 */
+                    double dfd = dsig * sigmoid(fs[i]);
+                    double dfc[3];
+                    for (int a = 0; a < 3; ++a) dfc[a] = dcol[a] * col[3 * i + a] * (1.0 - col[3 * i + a]);
+                    tgo_query_backward(3, res, od, 1, 1, xs + 3 * i, &dfd, NULL, dgrad, NULL);
+                    tgo_query_backward(3, res, oc, 3, 1, xs + 3 * i, dfc, NULL, cgrad, NULL);
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) rgb_out[3 * r + a] = C[a];
+        if (target)
+            for (int a = 0; a < 3; ++a) total += (C[a] - (double)target[3 * r + a]) * (C[a] - (double)target[3 * r + a]);
+    }
+    if (loss) *loss = total / (double)R;
+    free(sig); free(fs); free(col); free(del); free(Tr); free(xs);
+}

@@ -1,0 +1,442 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Every check here is independent of the oracle's own formulas: a library
+routine (torch grid_sample, torch.optim.Adam), a closed form (polynomial
+reproduction, homogeneous-medium transmittance, analytic SDFs), an invariant
+(face continuity, linearity) or finite differences. Each is chosen so that a
+plausible slip in the oracle (dropped 1/2, wrong corner bit, swapped Hessian
+entry, wrong sign in the compositing derivative) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+# --------------------------------------------------------------------------
+# Generator
+# --------------------------------------------------------------------------
+def test_splitmix64_published_vector():
+    vals = [int(l) for l in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt")) if l.strip() and l[0] != "#"]
+    st = np.uint64(1234567)
+    got = []
+    for _ in range(5):
+        got.append(int(W.splitmix64(np.asarray([st]))[0]))
+        with np.errstate(over="ignore"):
+            st = np.uint64(st + np.uint64(0x9E3779B97F4A7C15))
+    assert got == vals
+
+
+def test_oracle_uniform_matches_input_generator():
+    idx = np.arange(64, dtype=np.uint64)
+    a = W.uniform(7, 11, idx).astype(np.float64)
+    b = np.array([oracle.uniform(7, 11, int(i)) for i in idx])
+    assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# Eq. 2: the index rule
+# --------------------------------------------------------------------------
+def test_locate_rule_edges():
+    res = 5
+    pts = np.array([[0.0], [1.0], [0.25], [0.2499999], [-0.5], [1.5], [np.nan], [0.999]], np.float32)
+    cells, ts = oracle.locate(1, res, pts)
+    assert cells[:, 0].tolist() == [0, 3, 1, 0, 0, 3, 0, 3]
+    assert ts[0, 0] == 0.0 and ts[1, 0] == 1.0 and ts[2, 0] == 0.0
+    assert ts[4, 0] == 0.0 and ts[5, 0] == 1.0 and ts[6, 0] == 0.0
+    # t is the FP32 difference of the FP32 product
+    u = np.float32(np.float32(0.999) * np.float32(4.0))
+    assert ts[7, 0] == float(np.float32(u - np.float32(3.0)))
+
+
+# --------------------------------------------------------------------------
+# Order 0 is the linear grid (Sec. 4.1 "Linear only considers the zero-order
+# Taylor series"): the field must equal trilinear / bilinear interpolation.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,res,C", [(3, 5, 1), (3, 4, 3), (2, 6, 2)])
+def test_order0_equals_grid_sample(dim, res, C):
+    r = rng(1)
+    coefs = r.normal(size=res ** dim * C)
+    pts = r.random((300, dim)).astype(np.float32)
+    out, _, _, _ = oracle.query(dim, res, 0, C, coefs, pts, want_grad=False)
+    vol = torch.tensor(coefs.reshape((res,) * dim + (C,))).movedim(-1, 0)[None]   # (1, C, [D,] H, W)
+    g = torch.tensor(pts.astype(np.float64) * 2.0 - 1.0)
+    g = g.reshape((1,) + (1,) * (dim - 1) + (pts.shape[0], dim))
+    ref = torch.nn.functional.grid_sample(vol, g, mode="bilinear", align_corners=True)
+    ref = ref.reshape(C, -1).T.numpy()
+    np.testing.assert_allclose(out, ref, rtol=0, atol=2e-6 * np.abs(coefs).max())
+
+
+# --------------------------------------------------------------------------
+# Polynomial reproduction (Eq. 1 + the partition of unity of Eq. 4)
+# --------------------------------------------------------------------------
+def taylor_data_of_poly(dim, res, order, p, grad, hess):
+    """Exact Taylor data (grid units) of a polynomial at every vertex, exchange layout."""
+    h = 1.0 / (res - 1)
+    K = W.n_coefs(dim, order)
+    axes = np.meshgrid(*[np.arange(res) * h] * dim, indexing="ij")
+    X = np.stack([a.reshape(-1) for a in axes[::-1]], 1) if dim == 3 else None
+    # vertex v = x + res*(y + res*z): enumerate in that order
+    idx = np.arange(res ** dim)
+    coords = np.stack([(idx // res ** d) % res for d in range(dim)], 1) * h
+    out = np.zeros((res ** dim, K))
+    out[:, 0] = [p(c) for c in coords]
+    if order >= 1:
+        out[:, 1:1 + dim] = np.array([grad(c) for c in coords]) * h
+    if order >= 2:
+        Hs = np.array([hess(c) for c in coords]) * h * h
+        diag = [Hs[:, a, a] for a in range(dim)]
+        off = [Hs[:, 0, 1], Hs[:, 0, 2], Hs[:, 1, 2]] if dim == 3 else [Hs[:, 0, 1]]
+        out[:, 1 + dim:] = np.stack(diag + off, 1)
+    return out.reshape(-1)
+
+
+def quadratic(dim, seed):
+    r = rng(seed)
+    a = r.normal(); b = r.normal(size=dim); A = r.normal(size=(dim, dim)); A = A + A.T
+    p = lambda x: a + b @ x + 0.5 * x @ A @ x
+    return p, (lambda x: b + A @ x), (lambda x: A)
+
+
+@pytest.mark.parametrize("dim,res", [(3, 4), (3, 7), (2, 5)])
+def test_order2_reproduces_quadratics(dim, res):
+    p, gp, hp = quadratic(dim, 3 + dim)
+    coefs = taylor_data_of_poly(dim, res, 2, p, gp, hp)
+    pts = rng(4).random((500, dim)).astype(np.float32)
+    out, gx, _, _ = oracle.query(dim, res, 2, 1, coefs, pts)
+    x = pts.astype(np.float64)
+    np.testing.assert_allclose(out[:, 0], [p(v) for v in x], atol=5e-6)
+    np.testing.assert_allclose(gx[:, 0, :], [gp(v) for v in x], atol=5e-5)
+
+
+@pytest.mark.parametrize("dim,res", [(3, 5), (2, 4)])
+def test_order1_reproduces_affine(dim, res):
+    r = rng(5)
+    a, b = r.normal(), r.normal(size=dim)
+    coefs = taylor_data_of_poly(dim, res, 1, lambda x: a + b @ x, lambda x: b, None)
+    pts = r.random((400, dim)).astype(np.float32)
+    out, gx, _, _ = oracle.query(dim, res, 1, 1, coefs, pts)
+    np.testing.assert_allclose(out[:, 0], a + pts.astype(np.float64) @ b, atol=5e-6)
+    np.testing.assert_allclose(gx[:, 0, :], np.broadcast_to(b, (400, dim)), atol=5e-6)
+
+
+def test_order1_does_not_reproduce_quadratics():
+    p, gp, hp = quadratic(3, 9)
+    coefs = taylor_data_of_poly(3, 4, 1, p, gp, None)
+    pts = rng(6).random((200, 3)).astype(np.float32)
+    out, _, _, _ = oracle.query(3, 4, 1, 1, coefs, pts, want_grad=False)
+    assert np.abs(out[:, 0] - [p(v) for v in pts.astype(np.float64)]).max() > 1e-3
+
+
+def test_order2_does_not_reproduce_cubics():
+    res = 4
+    p = lambda x: x[0] ** 3
+    coefs = taylor_data_of_poly(3, res, 2, p, lambda x: np.array([3 * x[0] ** 2, 0, 0]),
+                                lambda x: np.diag([6 * x[0], 0, 0]))
+    pts = rng(7).random((200, 3)).astype(np.float32)
+    out, _, _, _ = oracle.query(3, res, 2, 1, coefs, pts, want_grad=False)
+    assert np.abs(out[:, 0] - pts[:, 0].astype(np.float64) ** 3).max() > 1e-5
+
+
+def test_order0_reproduces_multilinear():
+    r = rng(8)
+    c = r.normal(size=8)
+    p = lambda x: (c[0] + c[1] * x[0] + c[2] * x[1] + c[3] * x[2] + c[4] * x[0] * x[1]
+                   + c[5] * x[0] * x[2] + c[6] * x[1] * x[2] + c[7] * x[0] * x[1] * x[2])
+    coefs = taylor_data_of_poly(3, 2, 0, p, None, None)       # one cell: exact
+    pts = r.random((300, 3)).astype(np.float32)
+    out, _, _, _ = oracle.query(3, 2, 0, 1, coefs, pts, want_grad=False)
+    np.testing.assert_allclose(out[:, 0], [p(v) for v in pts.astype(np.float64)], atol=5e-6)
+
+
+def test_zero_derivatives_reduce_to_order0():
+    r = rng(9)
+    res, C = 4, 2
+    f0 = r.normal(size=(res ** 3, C))
+    c2 = np.zeros((res ** 3, C, 10)); c2[:, :, 0] = f0
+    pts = r.random((300, 3)).astype(np.float32)
+    a, ga, _, _ = oracle.query(3, res, 2, C, c2.reshape(-1), pts)
+    b, gb, _, _ = oracle.query(3, res, 0, C, f0.reshape(-1), pts)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+    np.testing.assert_allclose(ga, gb, atol=1e-11)
+
+
+def test_hessian_offdiagonal_order():
+    """A pure H_xz coefficient at every vertex gives the field x z h^{-2}-scaled cross term only."""
+    res = 3
+    h = 1.0 / (res - 1)
+    p = lambda x: x[0] * x[2]
+    coefs = taylor_data_of_poly(3, res, 2, p, lambda x: np.array([x[2], 0.0, x[0]]),
+                                lambda x: np.array([[0, 0, 1.0], [0, 0, 0], [1.0, 0, 0]]))
+    c = coefs.reshape(-1, 10)
+    assert np.allclose(c[:, 8], h * h) and np.allclose(c[:, 7], 0) and np.allclose(c[:, 9], 0)
+    pts = rng(10).random((100, 3)).astype(np.float32)
+    out, _, _, _ = oracle.query(3, res, 2, 1, coefs, pts, want_grad=False)
+    np.testing.assert_allclose(out[:, 0], pts[:, 0].astype(np.float64) * pts[:, 2], atol=5e-6)
+
+
+# --------------------------------------------------------------------------
+# Continuity across cell faces (Eq. 4 weights vanish off the face)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_face_continuity(order):
+    r = rng(11 + order)
+    res, C = 4, 2
+    K = W.n_coefs(3, order)
+    coefs = r.normal(size=res ** 3 * C * K)
+    for axis in range(3):
+        for _ in range(10):
+            cell = r.integers(0, res - 2, size=3)          # both cell and cell+e_axis valid
+            t = r.random(3)
+            t_lo = t.copy(); t_lo[axis] = 1.0
+            t_hi = t.copy(); t_hi[axis] = 0.0
+            up = cell.copy(); up[axis] += 1
+            fa, _ = oracle.eval_cell(3, res, order, C, coefs, cell, t_lo)
+            fb, _ = oracle.eval_cell(3, res, order, C, coefs, up, t_hi)
+            np.testing.assert_allclose(fa, fb, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Spatial gradient: central finite differences inside a cell
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,order", [(3, 2), (3, 1), (2, 2), (3, 0)])
+def test_spatial_gradient_finite_differences(dim, order):
+    r = rng(20 + order + dim)
+    res, C = 4, 2
+    coefs = r.normal(size=res ** dim * C * W.n_coefs(dim, order))
+    eps = 1e-5
+    for _ in range(20):
+        cell = r.integers(0, res - 1, size=dim)
+        t = 0.1 + 0.8 * r.random(dim)
+        _, gu = oracle.eval_cell(dim, res, order, C, coefs, cell, t)
+        for a in range(dim):
+            tp = t.copy(); tp[a] += eps
+            tm = t.copy(); tm[a] -= eps
+            fp, _ = oracle.eval_cell(dim, res, order, C, coefs, cell, tp)
+            fm, _ = oracle.eval_cell(dim, res, order, C, coefs, cell, tm)
+            np.testing.assert_allclose(gu[:, a], (fp - fm) / (2 * eps), atol=1e-8)
+
+
+def test_query_gradient_is_world_units():
+    r = rng(30)
+    res = 6
+    coefs = r.normal(size=res ** 3 * 10)
+    pts = r.random((50, 3)).astype(np.float32)
+    _, gx, cells, ts = oracle.query(3, res, 2, 1, coefs, pts, want_cells=True)
+    for n in range(50):
+        _, gu = oracle.eval_cell(3, res, 2, 1, coefs, cells[n], ts[n])
+        np.testing.assert_allclose(gx[n, 0], gu[0] * (res - 1), rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Coefficient gradient: central finite differences (exact by linearity)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,res,order,C", [(3, 2, 2, 1), (3, 3, 1, 2), (3, 4, 2, 1), (2, 3, 2, 2), (3, 3, 0, 3)])
+def test_coef_gradient_finite_differences(dim, res, order, C):
+    r = rng(40 + res + order)
+    K = W.n_coefs(dim, order)
+    coefs = r.normal(size=res ** dim * C * K)
+    N = 40
+    pts = r.random((N, dim)).astype(np.float32)
+    pts[0] = 0.0; pts[1] = 1.0                          # domain corners
+    dLdf = r.normal(size=(N, C)); dLdg = r.normal(size=(N, C, dim))
+
+    def L(c):
+        f, g, _, _ = oracle.query(dim, res, order, C, c, pts)
+        return float((f * dLdf).sum() + (g * dLdg).sum())
+
+    grad = oracle.query_backward(dim, res, order, C, pts, dLdf, dLdg)
+    eps = 1e-3
+    fd = np.zeros_like(coefs)
+    for j in range(coefs.size):
+        e = np.zeros_like(coefs); e[j] = eps
+        fd[j] = (L(coefs + e) - L(coefs - e)) / (2 * eps)
+    np.testing.assert_allclose(grad, fd, atol=1e-8 * max(1.0, np.abs(fd).max()))
+
+
+def test_adjoint_identity():
+    r = rng(50)
+    res, order, C, dim = 6, 2, 2, 3
+    K = W.n_coefs(dim, order)
+    theta = r.normal(size=res ** 3 * C * K)
+    pts = r.random((2000, 3)).astype(np.float32)
+    g = r.normal(size=(2000, C))
+    f, _, _, _ = oracle.query(dim, res, order, C, theta, pts, want_grad=False)
+    At_g = oracle.query_backward(dim, res, order, C, pts, g)
+    assert abs((f * g).sum() - theta @ At_g) < 1e-9 * abs(theta @ At_g) + 1e-9
+
+
+# --------------------------------------------------------------------------
+# Adam: torch.optim.Adam in float64
+# --------------------------------------------------------------------------
+def test_adam_matches_torch():
+    r = rng(60)
+    n = 1000
+    p0 = r.normal(size=n)
+    p = p0.copy(); m = np.zeros(n); v = np.zeros(n)
+    tp = torch.tensor(p0, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
+    for step in range(1, 6):
+        g = r.normal(size=n)
+        gg = g.copy()
+        oracle.adam(p, gg, m, v, 3e-3, 0.9, 0.999, 1e-8, step)
+        assert not gg.any()
+        tp.grad = torch.tensor(g)
+        opt.step()
+        np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# SDF targets and the SDF step (Sec. 3.2)
+# --------------------------------------------------------------------------
+def test_sdf_closed_forms():
+    sph = np.array([[0.5, 0.5, 0.5, 0.3]], np.float32)
+    box = np.array([[0.2, 0.3, 0.4, 0.1, 0.05, 0.2]], np.float32)
+    none_s = np.zeros((0, 4), np.float32); none_b = np.zeros((0, 6), np.float32)
+    f32 = lambda v: float(np.float32(v))
+    # sphere: centre, surface, outside
+    d = oracle.sdf_union(sph, none_b, np.array([[0.5, 0.5, 0.5], [0.8, 0.5, 0.5], [0.5, 0.5, 1.0]]))
+    np.testing.assert_allclose(d, [-f32(0.3), 0.8 - 0.5 - f32(0.3), 1.0 - 0.5 - f32(0.3)], atol=1e-12)
+    c = np.array([f32(0.2), f32(0.3), f32(0.4)]); h = np.array([f32(0.1), f32(0.05), f32(0.2)])
+    pts = np.array([c,                                  # centre: -min half extent
+                    c + [h[0] + 0.1, 0, 0],             # outside a face
+                    c + [h[0] + 0.03, h[1] + 0.04, 0],  # outside an edge
+                    c + h + [0.01, 0.02, 0.02],         # outside a corner
+                    c + [0, h[1] - 0.01, 0]])           # inside near a face
+    want = [-h.min(), 0.1, 0.05, 0.03, -0.01]
+    np.testing.assert_allclose(oracle.sdf_union(none_s, box, pts), want, atol=1e-12)
+    # union = min
+    both = oracle.sdf_union(sph, box, pts)
+    np.testing.assert_allclose(both, np.minimum(oracle.sdf_union(sph, none_b, pts), want), atol=1e-12)
+
+
+def test_box_sdf_brute_force():
+    box = np.array([[0.5, 0.45, 0.55, 0.2, 0.1, 0.15]], np.float32)
+    c = box[0, :3].astype(np.float64); h = box[0, 3:].astype(np.float64)
+    g = np.linspace(-1, 1, 121)
+    A, B = np.meshgrid(g, g, indexing="ij")
+    surf = []
+    for ax in range(3):
+        a1, a2 = (ax + 1) % 3, (ax + 2) % 3
+        for s in (-1, 1):
+            P = np.zeros((A.size, 3))
+            P[:, ax] = c[ax] + s * h[ax]; P[:, a1] = c[a1] + A.ravel() * h[a1]; P[:, a2] = c[a2] + B.ravel() * h[a2]
+            surf.append(P)
+    surf = np.concatenate(surf)
+    x = rng(70).random((60, 3))
+    inside = np.all(np.abs(x - c) < h, axis=1)
+    brute = np.array([np.linalg.norm(surf - p, axis=1).min() for p in x]) * np.where(inside, -1, 1)
+    got = oracle.sdf_union(np.zeros((0, 4), np.float32), box, x)
+    np.testing.assert_allclose(got, brute, atol=2.5e-3)
+
+
+def test_sdf_step_loss_gradient_finite_differences():
+    r = rng(80)
+    res, order = 3, 2
+    coefs = r.normal(size=res ** 3 * 10) * 0.2
+    shape = W.sphere_shape((0.45, 0.5, 0.55), 0.3)
+    pts = r.random((64, 3)).astype(np.float32)
+    lam = 0.1
+    g, _ = oracle.sdf_step(res, order, coefs, pts, shape.spheres, shape.boxes, lam)
+
+    def L(c):
+        _, (l1, eik) = oracle.sdf_step(res, order, c, pts, shape.spheres, shape.boxes, lam)
+        return l1 + lam * eik
+
+    eps = 1e-6
+    for j in r.choice(coefs.size, 40, replace=False):
+        e = np.zeros_like(coefs); e[j] = eps
+        fd = (L(coefs + e) - L(coefs - e)) / (2 * eps)
+        assert abs(fd - g[j]) < 1e-6 + 1e-5 * abs(fd), (j, fd, g[j])
+
+
+def test_sdf_step_loss_values():
+    """With the exact Taylor data of an affine SDF-like field the residual and the eikonal term are known."""
+    res = 5
+    b = np.array([0.6, 0.0, 0.8])                         # |b| = 1: eikonal term zero
+    coefs = taylor_data_of_poly(3, res, 2, lambda x: -0.2 + b @ x, lambda x: b, lambda x: np.zeros((3, 3)))
+    sph = np.array([[0.5, 0.5, 0.5, 0.25]], np.float32)
+    pts = rng(81).random((100, 3)).astype(np.float32)
+    _, (l1, eik) = oracle.sdf_step(res, 2, coefs, pts, sph, np.zeros((0, 6), np.float32), 0.1)
+    x = pts.astype(np.float64)
+    d = np.linalg.norm(x - 0.5, axis=1) - np.float32(0.25)
+    np.testing.assert_allclose(l1, np.abs(-0.2 + x @ b - d).mean(), atol=1e-6)
+    assert eik < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Volume rendering (Sec. 3.3, Eq. 10 / Eq. 11)
+# --------------------------------------------------------------------------
+def sp(x):
+    return math.log1p(math.exp(x))
+
+
+def sg(x):
+    return 1.0 / (1.0 + math.exp(-x))
+
+
+def test_render_homogeneous_closed_form():
+    res = 4
+    f0, g0 = 0.7, -0.3
+    dco = np.full(res ** 3, f0)                           # order 0 density
+    cco = np.tile([g0, 0.1, 0.9], res ** 3)               # order 0 colour, 3 channels
+    o = np.array([[-0.5, 0.5, 0.5], [0.3, -1.0, 0.4], [2.0, 2.0, 2.0], [0.5, 0.5, 0.5]], np.float32)
+    d = np.array([[1, 0, 0], [0.1, 1, 0.05], [1, 0, 0], [0, 0, 1]], np.float64)
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    rgb = oracle.render(res, 0, dco, 0, cco, o, d, S=64, seed=3, bg=1.0)
+    sigma = sp(f0)
+    for r in range(4):
+        hit, n, f = oracle.ray_box(o[r].astype(np.float64), d[r].astype(np.float64))
+        if not hit:
+            np.testing.assert_allclose(rgb[r], [1, 1, 1]); continue
+        # stratified samples: delta_i = t_{i+1} - t_i with t_S = far, so the
+        # optical depth covers [t_0, far], t_0 = near + xi_0 (far - near) / S
+        t0 = n + float(W.uniform(3, r, 0)) * (f - n) / 64
+        T = math.exp(-sigma * (f - t0))
+        want = [sg(c) * (1 - T) + T for c in (g0, 0.1, 0.9)]
+        np.testing.assert_allclose(rgb[r], want, rtol=1e-12)
+    assert not oracle.ray_box(o[2].astype(np.float64), d[2].astype(np.float64))[0]
+
+
+def test_render_black_background_is_eq10():
+    """bg = 0 leaves exactly the sum of Eq. 10; a dense medium saturates to the colour."""
+    res = 3
+    dco = np.full(res ** 3, 40.0); cco = np.tile([0.0, 2.0, -2.0], res ** 3)
+    o = np.array([[-1.0, 0.5, 0.5]], np.float32); d = np.array([[1.0, 0.0, 0.0]], np.float32)
+    rgb = oracle.render(res, 0, dco, 0, cco, o, d, S=16, seed=1, bg=0.0)
+    np.testing.assert_allclose(rgb[0], [sg(0.0), sg(2.0), sg(-2.0)], rtol=1e-12)
+
+
+def test_render_gradient_finite_differences():
+    r = rng(90)
+    res, od, oc = 3, 2, 1
+    dco = r.normal(size=res ** 3 * 10) * 0.5
+    cco = r.normal(size=res ** 3 * 3 * 4) * 0.5
+    o, d = W.random_rays(5, 3, radius=1.2, spread=0.3)
+    tgt = r.random((3, 3)).astype(np.float32)
+    S = 12
+    _, loss, dg, cg = oracle.render(res, od, dco, oc, cco, o, d, S, seed=9, target=tgt)
+
+    def L(a, b):
+        return oracle.render(res, od, a, oc, b, o, d, S, seed=9, target=tgt)[1]
+
+    eps = 1e-6
+    for j in r.choice(dco.size, 25, replace=False):
+        e = np.zeros_like(dco); e[j] = eps
+        fd = (L(dco + e, cco) - L(dco - e, cco)) / (2 * eps)
+        assert abs(fd - dg[j]) < 1e-7 + 1e-5 * abs(fd), ("density", j, fd, dg[j])
+    for j in r.choice(cco.size, 25, replace=False):
+        e = np.zeros_like(cco); e[j] = eps
+        fd = (L(dco, cco + e) - L(dco, cco - e)) / (2 * eps)
+        assert abs(fd - cg[j]) < 1e-7 + 1e-5 * abs(fd), ("colour", j, fd, cg[j])
