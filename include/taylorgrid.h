@@ -1,0 +1,210 @@
+/*
+ * taylorgrid.h - C ABI of the GB300 TaylorGrid field engine.
+ *
+ * TaylorGrid (arXiv 2402.14415, Sec. 3.1) stores at every vertex of a dense
+ * grid V_T a truncated Taylor series S(v) of the field: the value, the
+ * gradient and, at order 2, the Hessian. A query point x is evaluated by
+ * finding its voxel (Eq. 2), evaluating the series of each of the 2^D corner
+ * vertices at the offset x - v_i (Eq. 1, Eq. 3) and blending the 2^D values
+ * with trilinear (bilinear in 2-D) weights (Eq. 4). The grid is optimised
+ * directly: the loss gradient is scattered back onto the coefficients.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Domain [0,1]^D with D = dim in {2, 3}; `res` >= 2 vertices per axis,
+ *    vertex j at x = j / (res - 1).
+ *  - K = C(D + order, order) coefficients per vertex and channel, stored in
+ *    this order (true Hessian entries; the 1/2 of Eq. 1 applies to the
+ *    diagonal only and each off-diagonal entry appears once):
+ *        3-D: f, g_x, g_y, g_z, H_xx, H_yy, H_zz, H_xy, H_xz, H_yz
+ *        2-D: f, g_x, g_y, H_xx, H_yy, H_xy
+ *    Derivatives are taken with respect to grid units u = x (res - 1): the
+ *    offset of Eq. 3 is delta = t - b_i in [-1, 1]^D.
+ *  - Exchange layout (tg_set_coefs / tg_get_coefs / coefficient gradients):
+ *    FP32 [vertex][channel][k], vertex = x + res (y + res z). The library's
+ *    device layout of the stored coefficients is the same order, in the
+ *    grid's storage dtype.
+ *  - Index rule of Eq. 2 (bit-exact, normative): clamp each coordinate to
+ *    [0,1] (NaN becomes 0), u = fl32(x * (res - 1)) as one round-to-nearest
+ *    FP32 multiply, c = min(floor(u), res - 2), t = fl32(u - c). A point on an
+ *    interior face belongs to the upper cell; x = 1 lies in cell res - 2, t = 1.
+ *  - All evaluation, blending and gradient accumulation is FP32.
+ *  - Pointers marked (device) are device memory owned by the caller unless a
+ *    call says otherwise; (host) pointers are host memory. Every call that
+ *    takes a `tg_stream` (a cudaStream_t; NULL = the legacy default stream)
+ *    only enqueues work on that stream and returns without synchronising.
+ *  - Every call returns a tg_status and never aborts. A failed call leaves
+ *    its outputs unspecified; tg_last_error() describes the last failure of
+ *    the calling thread.
+ */
+#ifndef TAYLORGRID_H
+#define TAYLORGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TG_API __attribute__((visibility("default")))
+#else
+#define TG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TG_OK = 0,
+    TG_EINVAL = 1,     /* an argument is out of range or a pointer is NULL */
+    TG_ENOMEM = 2,     /* device allocation failed */
+    TG_EBUDGET = 3,    /* admission refused: the request can never fit the HBM budget */
+    TG_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    TG_EDEVICE = 5,    /* a CUDA call or kernel launch failed */
+    TG_ENOTFOUND = 6,  /* unknown job or handle */
+    TG_EBUSY = 7       /* the object is in use (e.g. a grid still referenced by a job) */
+} tg_status;
+
+typedef enum { TG_F32 = 0, TG_BF16 = 1, TG_F16 = 2 } tg_dtype;
+
+typedef void *tg_stream;            /* cudaStream_t */
+typedef struct tg_grid tg_grid;     /* opaque, library-owned */
+
+/* Human-readable name of a status code (static storage). */
+TG_API const char *tg_status_string(tg_status s);
+
+/* Description of the last failure on the calling thread (static, per thread). */
+TG_API const char *tg_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Grid storage V_T (Sec. 3.1: "a dense grid G of size w x d x h", each vertex
+ * storing the low-order Taylor series).
+ * ------------------------------------------------------------------------ */
+
+/* Create a res^dim grid of order `order` (0, 1 or 2) with `channels`
+ * (1..4) independent series per vertex, stored in `dtype`. When dtype is
+ * BF16 or FP16 an FP32 master copy is kept for the optimiser and the stored
+ * copy is its round-to-nearest image. Coefficients are initialised to
+ * N(0, init_std^2) drawn from the counter-based generator
+ * (seed, stream 0xC0EF, index j) in exchange-layout order, on the current
+ * device, and the call synchronises the device before returning.
+ * Errors: TG_EINVAL for a bad shape or NULL `out`, TG_ENOMEM. */
+TG_API tg_status tg_create(int dim, int res, int order, int channels, tg_dtype dtype,
+                    uint64_t seed, float init_std, tg_grid **out);
+
+/* Free a grid and everything it owns (coefficients, master, Adam state).
+ * The caller must ensure no enqueued work still uses it. NULL is a no-op. */
+TG_API tg_status tg_destroy(tg_grid *grid);
+
+typedef struct {
+    int dim, res, order, channels, K;
+    tg_dtype dtype;
+    int64_t n_vertices;     /* res^dim */
+    int64_t n_coefs;        /* n_vertices * channels * K */
+    size_t bytes;           /* device bytes held (storage + master + Adam state) */
+    const void *coefs;      /* (device) stored coefficients, storage dtype, exchange order */
+    const float *master;    /* (device) FP32 master (same as coefs for TG_F32) */
+} tg_grid_info;
+
+TG_API tg_status tg_get_info(const tg_grid *grid, tg_grid_info *info);
+
+/* Load FP32 coefficients (device, exchange layout, n_coefs floats) into the
+ * master copy and the stored copy (rounded to the storage dtype). */
+TG_API tg_status tg_set_coefs(tg_grid *grid, const float *src, tg_stream stream);
+
+/* Read coefficients into `dst` (device, n_coefs floats). which = 0: the
+ * stored copy, widened to FP32 (what queries use); which = 1: the FP32 master. */
+TG_API tg_status tg_get_coefs(const tg_grid *grid, float *dst, int which, tg_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Field query, Eq. 2 - Eq. 4.
+ * ------------------------------------------------------------------------ */
+
+/* Eq. 2 alone: the voxel of each point under the index rule above.
+ * Writes cells (device, N x dim int32, lower-corner vertex coordinates) and,
+ * if t is not NULL, the local coordinates (device, N x dim FP32). These are
+ * exactly the indices and offsets every query kernel uses. */
+TG_API tg_status tg_locate(int dim, int res, const float *pts, int64_t N, int32_t *cells, float *t,
+                    tg_stream stream);
+
+/* Forward query of N points (device, N x dim FP32, row-major). Writes
+ * out (device, N x channels) = f(x) and, if grad_x is not NULL, the spatial
+ * gradient in world units (device, N x channels x dim) = d f / d x, which is
+ * the blend derivative of Eq. 4 plus the series derivative g + H delta of
+ * each corner, times (res - 1). Points are clamped to the domain.
+ * N = 0 is a no-op. Errors: TG_EINVAL (NULL grid/pts/out with N > 0,
+ * N < 0), TG_EDEVICE (launch failure). */
+TG_API tg_status tg_query(const tg_grid *grid, const float *pts, int64_t N,
+                   float *out, float *grad_x, tg_stream stream);
+
+/* Coefficient gradient of the query (direct grid optimisation: the field is
+ * linear in the coefficients, f = A theta, so this computes A^T). Given the
+ * upstream gradients dL_df (device, N x channels) and optionally dL_dgradx
+ * (device, N x channels x dim, world units; NULL = none), ADDS
+ *   dL/dtheta_{v,c,k} += sum_n w_i(t_n) phi_k(delta_i) dL_df[n,c]
+ *                        + (res-1) sum_d dL_dgradx[n,c,d] d/du_d(w_i phi_k)
+ * into coef_grad (device, FP32, n_coefs, exchange layout) with FP32 atomics;
+ * consecutive points that share a cell are first combined inside the warp.
+ * The caller zeroes coef_grad (tg_adam_step does so after using it).
+ * Errors as tg_query. */
+TG_API tg_status tg_query_backward(const tg_grid *grid, const float *pts, int64_t N,
+                            const float *dL_df, const float *dL_dgradx,
+                            float *coef_grad, tg_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Brick-binned query path. The paper gives no kernel design; this is the
+ * GB300 path for large batches: points are counting-sorted by the 8^D-cell
+ * brick that holds their voxel, then each thread block stages one brick of
+ * coefficients in shared memory and evaluates (forward) or accumulates
+ * (backward) its points there, so the grid is streamed about once per pass
+ * instead of gathered per point. Results equal tg_query / tg_query_backward.
+ * ------------------------------------------------------------------------ */
+typedef struct tg_batch tg_batch;   /* opaque; owns the scratch of one binned batch */
+
+/* Create a batch able to hold up to max_points points for grids of the
+ * given dim and res (the brick count depends on res). Allocates device
+ * scratch (about 24 bytes per point plus 8 bytes per brick). */
+TG_API tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out);
+TG_API tg_status tg_batch_destroy(tg_batch *batch);
+
+/* Bin N points (device, N x dim). The batch keeps a sorted copy of the points
+ * and the permutation; `pts` may be reused by the caller afterwards. */
+TG_API tg_status tg_batch_bin(tg_batch *batch, const float *pts, int64_t N, tg_stream stream);
+
+/* Same outputs as tg_query / tg_query_backward for the points last binned
+ * (outputs and upstream gradients in the caller's original point order). */
+TG_API tg_status tg_query_binned(const tg_grid *grid, const tg_batch *batch,
+                          float *out, float *grad_x, tg_stream stream);
+TG_API tg_status tg_query_backward_binned(const tg_grid *grid, const tg_batch *batch,
+                                   const float *dL_df, const float *dL_dgradx,
+                                   float *coef_grad, tg_stream stream);
+
+/* The binned kernels wait on their TMA copies with a 2 s limit; a wait that
+ * gives up sets a device flag instead of hanging. Synchronously reads that
+ * flag into *timed_out (non-zero = some launch since the last call gave up,
+ * its outputs are invalid) and clears it. */
+TG_API tg_status tg_batch_timeouts(tg_batch *batch, int *timed_out);
+
+/* ---------------------------------------------------------------------------
+ * Optimiser. The paper fixes only the learning rate (Sec. 4.1, "fixed
+ * learning rate of 0.003"); the engine uses Adam (Kingma & Ba 2015) with
+ * bias correction and no weight decay, fused into one pass.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    float lr;
+    float beta1, beta2, eps;
+    int64_t step;            /* 1-based step number used for bias correction */
+} tg_adam;
+
+/* One fused Adam step over every coefficient of the grid: reads the FP32
+ * master, coef_grad (device, n_coefs) and the moments, writes master and
+ * moments, refreshes the stored BF16/FP16 copy (round to nearest even) and
+ * zeroes coef_grad. The first call on a grid allocates and zeroes the
+ * moments (synchronously), so make it before any stream capture.
+ * Errors: TG_EINVAL (NULL, step < 1), TG_ENOMEM, TG_EDEVICE. */
+TG_API tg_status tg_adam_step(tg_grid *grid, float *coef_grad, const tg_adam *params, tg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TAYLORGRID_H */

@@ -211,7 +211,9 @@ TGO_API void tgo_query(int dim, int res, int order, int C, const double *coefs, 
  * the field is linear in the coefficients, so dL/dtheta = J^T dL/df with
  * J_{n,(i,k)} = w_i(t) phi_k(delta_i), plus the same for the spatial gradient
  * with d/du of (w_i phi_k). Accumulates into coef_grad; abs_grad (optional)
- * accumulates |contribution| for the scale-aware tolerance. */
+ * accumulates the sum of the absolute values of the individual terms of each
+ * contribution (the magnitude FP32 rounding of that sum is relative to), for
+ * the scale-aware tolerance. */
 TGO_API void tgo_query_backward(int dim, int res, int order, int C, int64_t N, const float *pts,
                                 const double *dL_df, const double *dL_dgx,
                                 double *coef_grad, double *abs_grad)
@@ -233,14 +235,18 @@ TGO_API void tgo_query_backward(int dim, int res, int order, int C, int64_t N, c
             for (int ch = 0; ch < C; ++ch) {
                 for (int k = 0; k < K; ++k) {
                     double c = w * phi[k] * dL_df[n * C + ch];
+                    double mag = fabs(c);   /* sum of |terms|: the scale FP32 rounding acts on */
                     if (dL_dgx)
-                        for (int a = 0; a < dim; ++a)
-                            c += hinv * dL_dgx[(n * C + ch) * dim + a] * (dw[a] * phi[k] + w * dphi[k][a]);
+                        for (int a = 0; a < dim; ++a) {
+                            double ga = hinv * dL_dgx[(n * C + ch) * dim + a];
+                            c += ga * (dw[a] * phi[k] + w * dphi[k][a]);
+                            mag += fabs(ga) * (fabs(dw[a] * phi[k]) + fabs(w * dphi[k][a]));
+                        }
                     int64_t j = (v * C + ch) * K + k;
                     #pragma omp atomic
                     coef_grad[j] += c;
                     if (abs_grad) {
-                        double a = fabs(c);
+                        double a = mag;
                         #pragma omp atomic
                         abs_grad[j] += a;
                     }

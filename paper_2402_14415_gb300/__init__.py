@@ -1,0 +1,17 @@
+"""GB300-native TaylorGrid field engine (arXiv 2402.14415).
+
+The CUDA library ``libtaylorgrid.so`` (sources in ``csrc/``, ABI in
+``include/taylorgrid.h``) holds every kernel of the path; this package is
+its thin Python binding (``binding``) plus torch.autograd wrappers
+(``autograd``). There is no CPU fallback.
+"""
+from .binding import (  # noqa: F401
+    TG_BF16, TG_F16, TG_F32, Batch, Grid, TGError, exported_symbols, load, tg_adam_step, tg_batch_bin,
+    tg_batch_create, tg_batch_timeouts, tg_create, tg_get_coefs, tg_locate, tg_query, tg_query_backward,
+    tg_query_backward_binned, tg_query_binned, tg_set_coefs,
+)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from .builder import build as _build
+    return _build(force=force, verbose=verbose)

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of ``libtaylorgrid.so`` (the C ABI in include/taylorgrid.h).
+
+Argument marshalling only: every step of the TaylorGrid path runs in the
+library's CUDA kernels. Tensors are torch CUDA tensors used as device memory;
+the stream is torch's current stream unless one is given. There is no CPU
+fallback: without the built library or a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtaylorgrid.so")
+
+TG_F32, TG_BF16, TG_F16 = 0, 1, 2
+DTYPES = {"f32": TG_F32, "fp32": TG_F32, "float32": TG_F32, "bf16": TG_BF16, "bfloat16": TG_BF16,
+          "f16": TG_F16, "fp16": TG_F16, "float16": TG_F16}
+STATUS = {0: "TG_OK", 1: "TG_EINVAL", 2: "TG_ENOMEM", 3: "TG_EBUDGET", 4: "TG_ETIMEOUT", 5: "TG_EDEVICE",
+          6: "TG_ENOTFOUND", 7: "TG_EBUSY"}
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+class TGError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [("dim", _int), ("res", _int), ("order", _int), ("channels", _int), ("K", _int),
+                ("dtype", _int), ("n_vertices", _i64), ("n_coefs", _i64), ("bytes", ctypes.c_size_t),
+                ("coefs", _vp), ("master", _vp)]
+
+
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", _i64)]
+
+
+# name -> argtypes (restype is tg_status = int unless noted)
+_SIGS = {
+    "tg_create": [_int, _int, _int, _int, _int, ctypes.c_uint64, ctypes.c_float, ctypes.POINTER(_vp)],
+    "tg_destroy": [_vp],
+    "tg_get_info": [_vp, ctypes.POINTER(GridInfo)],
+    "tg_set_coefs": [_vp, _vp, _vp],
+    "tg_get_coefs": [_vp, _vp, _int, _vp],
+    "tg_locate": [_int, _int, _vp, _i64, _vp, _vp, _vp],
+    "tg_query": [_vp, _vp, _i64, _vp, _vp, _vp],
+    "tg_query_backward": [_vp, _vp, _i64, _vp, _vp, _vp, _vp],
+    "tg_batch_create": [_int, _int, _i64, ctypes.POINTER(_vp)],
+    "tg_batch_destroy": [_vp],
+    "tg_batch_bin": [_vp, _vp, _i64, _vp],
+    "tg_query_binned": [_vp, _vp, _vp, _vp, _vp],
+    "tg_query_backward_binned": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "tg_batch_timeouts": [_vp, ctypes.POINTER(_int)],
+    "tg_adam_step": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
+}
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS) + ["tg_status_string", "tg_last_error"]
+
+
+def load():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _int
+        L.tg_status_string.argtypes = [_int]; L.tg_status_string.restype = ctypes.c_char_p
+        L.tg_last_error.argtypes = []; L.tg_last_error.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise TGError(status, where, (load().tg_last_error() or b"").decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t, name, dtype=torch.float32, numel=None, optional=False):
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the TaylorGrid library has no CPU path)")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+class Grid:
+    """Owning handle of a tg_grid (freed by close() or garbage collection)."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+        info = GridInfo()
+        _check(load().tg_get_info(handle, ctypes.byref(info)), "tg_get_info")
+        self.dim, self.res, self.order, self.channels, self.K = info.dim, info.res, info.order, info.channels, info.K
+        self.dtype = info.dtype
+        self.n_vertices, self.n_coefs = info.n_vertices, info.n_coefs
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("grid is closed")
+        return self._h
+
+    def info(self) -> GridInfo:
+        info = GridInfo()
+        _check(load().tg_get_info(self.handle, ctypes.byref(info)), "tg_get_info")
+        return info
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tg_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def tg_create(dim: int, res: int, order: int, channels: int = 1, dtype="f32", seed: int = 0,
+              init_std: float = 0.0) -> Grid:
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    h = _vp()
+    _check(load().tg_create(dim, res, order, channels, dt, seed, init_std, ctypes.byref(h)), "tg_create")
+    return Grid(h.value)
+
+
+def tg_set_coefs(grid: Grid, coefs: torch.Tensor, stream=None):
+    _check(load().tg_set_coefs(grid.handle, _ptr(coefs, "coefs", numel=grid.n_coefs), _stream(stream)), "tg_set_coefs")
+
+
+def tg_get_coefs(grid: Grid, out: torch.Tensor | None = None, which: int = 0, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(grid.n_coefs, device="cuda", dtype=torch.float32)
+    _check(load().tg_get_coefs(grid.handle, _ptr(out, "out", numel=grid.n_coefs), which, _stream(stream)), "tg_get_coefs")
+    return out
+
+
+def tg_locate(dim: int, res: int, pts: torch.Tensor, stream=None):
+    """Cells (N, dim) int32 and local coordinates (N, dim) float32 of Eq. 2."""
+    N = pts.shape[0]
+    cells = torch.empty((N, dim), device=pts.device, dtype=torch.int32)
+    t = torch.empty((N, dim), device=pts.device, dtype=torch.float32)
+    _check(load().tg_locate(dim, res, _ptr(pts, "pts", numel=N * dim), N, _ptr(cells, "cells", torch.int32),
+                            _ptr(t, "t"), _stream(stream)), "tg_locate")
+    return cells, t
+
+
+def tg_query(grid: Grid, pts: torch.Tensor, out=None, grad_x=None, want_grad=False, stream=None):
+    N = pts.shape[0]
+    if out is None:
+        out = torch.empty((N, grid.channels), device=pts.device, dtype=torch.float32)
+    if grad_x is None and want_grad:
+        grad_x = torch.empty((N, grid.channels, grid.dim), device=pts.device, dtype=torch.float32)
+    _check(load().tg_query(grid.handle, _ptr(pts, "pts", numel=N * grid.dim), N,
+                           _ptr(out, "out", numel=N * grid.channels),
+                           _ptr(grad_x, "grad_x", numel=N * grid.channels * grid.dim, optional=True),
+                           _stream(stream)), "tg_query")
+    return (out, grad_x) if (want_grad or grad_x is not None) else out
+
+
+def tg_query_backward(grid: Grid, pts, dL_df, coef_grad, dL_dgradx=None, stream=None):
+    N = pts.shape[0]
+    _check(load().tg_query_backward(grid.handle, _ptr(pts, "pts", numel=N * grid.dim), N,
+                                    _ptr(dL_df, "dL_df", numel=N * grid.channels),
+                                    _ptr(dL_dgradx, "dL_dgradx", numel=N * grid.channels * grid.dim, optional=True),
+                                    _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), _stream(stream)),
+           "tg_query_backward")
+    return coef_grad
+
+
+class Batch:
+    """Owning handle of a tg_batch (binned point batch)."""
+
+    def __init__(self, dim: int, res: int, max_points: int):
+        h = _vp()
+        _check(load().tg_batch_create(dim, res, max_points, ctypes.byref(h)), "tg_batch_create")
+        self._h = h.value
+        self.dim, self.res, self.max_points, self.n = dim, res, max_points, 0
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("batch is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tg_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def tg_batch_create(dim: int, res: int, max_points: int) -> Batch:
+    return Batch(dim, res, max_points)
+
+
+def tg_batch_bin(batch: Batch, pts: torch.Tensor, stream=None):
+    N = pts.shape[0]
+    _check(load().tg_batch_bin(batch.handle, _ptr(pts, "pts", numel=N * batch.dim), N, _stream(stream)), "tg_batch_bin")
+    batch.n = N
+    return batch
+
+
+def tg_query_binned(grid: Grid, batch: Batch, out=None, grad_x=None, want_grad=False, stream=None):
+    N = batch.n
+    dev = torch.device("cuda")
+    if out is None:
+        out = torch.empty((N, grid.channels), device=dev, dtype=torch.float32)
+    if grad_x is None and want_grad:
+        grad_x = torch.empty((N, grid.channels, grid.dim), device=dev, dtype=torch.float32)
+    _check(load().tg_query_binned(grid.handle, batch.handle, _ptr(out, "out", numel=N * grid.channels),
+                                  _ptr(grad_x, "grad_x", numel=N * grid.channels * grid.dim, optional=True),
+                                  _stream(stream)), "tg_query_binned")
+    return (out, grad_x) if (want_grad or grad_x is not None) else out
+
+
+def tg_query_backward_binned(grid: Grid, batch: Batch, dL_df, coef_grad, dL_dgradx=None, stream=None):
+    N = batch.n
+    _check(load().tg_query_backward_binned(grid.handle, batch.handle, _ptr(dL_df, "dL_df", numel=N * grid.channels),
+                                           _ptr(dL_dgradx, "dL_dgradx", numel=N * grid.channels * grid.dim,
+                                                optional=True),
+                                           _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), _stream(stream)),
+           "tg_query_backward_binned")
+    return coef_grad
+
+
+def tg_batch_timeouts(batch: Batch) -> int:
+    v = _int(0)
+    _check(load().tg_batch_timeouts(batch.handle, ctypes.byref(v)), "tg_batch_timeouts")
+    return v.value
+
+
+def tg_adam_step(grid: Grid, coef_grad, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    prm = AdamParams(lr, beta1, beta2, eps, step)
+    _check(load().tg_adam_step(grid.handle, _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), ctypes.byref(prm),
+                               _stream(stream)), "tg_adam_step")

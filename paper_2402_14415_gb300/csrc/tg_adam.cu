@@ -1,0 +1,126 @@
+// Fused Adam step over every coefficient of a grid (one HBM pass).
+// Reads master, gradient and both moments; writes master, moments, the
+// BF16/FP16 stored copy, and zeroes the gradient for the next step.
+#include "tg_internal.cuh"
+
+namespace tg {
+
+struct AdamCoef {
+    float beta1, beta2, one_m_b1, one_m_b2;
+    float step_size;       // lr / (1 - beta1^t)
+    float inv_sqrt_bc2;    // 1 / sqrt(1 - beta2^t)
+    float eps;
+};
+
+__device__ __forceinline__ float adam_one(float &p, float g, float &m, float &v, const AdamCoef &a)
+{
+    m = fmaf(a.beta1, m, a.one_m_b1 * g);
+    v = fmaf(a.beta2, v, a.one_m_b2 * g * g);
+    const float denom = fmaf(sqrtf(v), a.inv_sqrt_bc2, a.eps);   // sqrt(v_hat) + eps
+    p -= a.step_size * __fdividef(m, denom);
+    return p;
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T *dst, int64_t j, float a, float b, float c, float d);
+template <>
+__device__ __forceinline__ void store4<float>(float *, int64_t, float, float, float, float) {}
+template <>
+__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16 *dst, int64_t j, float a, float b, float c, float d)
+{
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&lo);
+    u.y = *reinterpret_cast<unsigned *>(&hi);
+    *reinterpret_cast<uint2 *>(dst + j) = u;
+}
+template <>
+__device__ __forceinline__ void store4<__half>(__half *dst, int64_t j, float a, float b, float c, float d)
+{
+    __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&lo);
+    u.y = *reinterpret_cast<unsigned *>(&hi);
+    *reinterpret_cast<uint2 *>(dst + j) = u;
+}
+
+// Vectorised body over n4 = n / 4 float4 groups, scalar tail handled by block 0.
+template <typename T>
+__global__ void __launch_bounds__(256)
+adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+            T *__restrict__ shadow, int64_t n, AdamCoef a)
+{
+    const int64_t n4 = n >> 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float4 *p4 = reinterpret_cast<float4 *>(p);
+    float4 *g4 = reinterpret_cast<float4 *>(g);
+    float4 *m4 = reinterpret_cast<float4 *>(m);
+    float4 *v4 = reinterpret_cast<float4 *>(v);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += stride) {
+        float4 pp = p4[j], gg = __ldcs(g4 + j), mm = m4[j], vv = v4[j];
+        adam_one(pp.x, gg.x, mm.x, vv.x, a);
+        adam_one(pp.y, gg.y, mm.y, vv.y, a);
+        adam_one(pp.z, gg.z, mm.z, vv.z, a);
+        adam_one(pp.w, gg.w, mm.w, vv.w, a);
+        p4[j] = pp;
+        m4[j] = mm;
+        v4[j] = vv;
+        __stcs(g4 + j, make_float4(0.f, 0.f, 0.f, 0.f));
+        if (shadow) store4<T>(shadow, 4 * j, pp.x, pp.y, pp.z, pp.w);
+    }
+    if (blockIdx.x == 0) {
+        for (int64_t j = 4 * n4 + threadIdx.x; j < n; j += blockDim.x) {
+            float pp = p[j], mm = m[j], vv = v[j];
+            adam_one(pp, g[j], mm, vv, a);
+            p[j] = pp; m[j] = mm; v[j] = vv; g[j] = 0.0f;
+            if (shadow) shadow[j] = from_f32<T>(pp);
+        }
+    }
+}
+
+}  // namespace tg
+
+using namespace tg;
+
+extern "C" tg_status tg_adam_step(tg_grid *g, float *grad, const tg_adam *prm, tg_stream stream)
+{
+    if (!g || !grad || !prm) return fail(TG_EINVAL, "tg_adam_step: NULL argument");
+    if (prm->step < 1) return fail(TG_EINVAL, "tg_adam_step: step must be >= 1");
+    if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
+        return fail(TG_EINVAL, "tg_adam_step: betas must lie in [0,1) and eps >= 0");
+    if (((uintptr_t)grad & 15) != 0) return fail(TG_EINVAL, "tg_adam_step: coef_grad must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g->adam_m) {
+        tg_status st = cuda_status(cudaMalloc(&g->adam_m, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(m)");
+        if (st == TG_OK) st = cuda_status(cudaMalloc(&g->adam_v, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(v)");
+        if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_m, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero m");
+        if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_v, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero v");
+        if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_adam_step: init moments");
+        if (st != TG_OK) {
+            cudaFree(g->adam_m); cudaFree(g->adam_v);
+            g->adam_m = g->adam_v = nullptr;
+            return st;
+        }
+    }
+    const double b1t = 1.0 - pow((double)prm->beta1, (double)prm->step);
+    const double b2t = 1.0 - pow((double)prm->beta2, (double)prm->step);
+    AdamCoef a;
+    a.beta1 = prm->beta1; a.beta2 = prm->beta2;
+    a.one_m_b1 = 1.0f - prm->beta1; a.one_m_b2 = 1.0f - prm->beta2;
+    a.step_size = (float)((double)prm->lr / b1t);
+    a.inv_sqrt_bc2 = (float)(1.0 / sqrt(b2t));
+    a.eps = prm->eps;
+    const int64_t n4 = g->ncoef / 4;
+    int per_sm = blocks_per_sm((const void *)adam_kernel<float>, 256, 0);
+    int64_t need = (n4 + 255) / 256;
+    int64_t cap = (int64_t)num_sms() * per_sm;
+    unsigned nb = (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
+    if (g->dtype == TG_F32)
+        adam_kernel<float><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, nullptr, g->ncoef, a);
+    else if (g->dtype == TG_BF16)
+        adam_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v,
+                                                      (__nv_bfloat16 *)g->store, g->ncoef, a);
+    else
+        adam_kernel<__half><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, (__half *)g->store, g->ncoef, a);
+    return launch_status("tg_adam_step");
+}

@@ -1,0 +1,85 @@
+"""GPU parity of the brick-binned path (TMA-staged forward, TMA reduce-add
+backward) against the FP64 oracle and against the point-parallel path."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from parity import check_coef_grad, check_forward, points, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [  # res, order, C, dtype  (res - 1 not a multiple of 8: ragged last brick)
+    (34, 2, 1, "f32"), (20, 1, 3, "f32"), (24, 0, 1, "f32"), (18, 2, 2, "f32"), (36, 2, 1, "bf16"),
+    (28, 1, 1, "f16"), (10, 2, 1, "f32"),
+]
+
+
+def clustered(n, seed=3):
+    """Dense clusters: several hundred points inside single bricks."""
+    r = np.random.default_rng(seed)
+    c = r.random((4, 3)) * 0.8 + 0.1
+    return np.concatenate([c[k] + 0.01 * r.standard_normal((n // 4, 3)) for k in range(4)]).astype(np.float32)
+
+
+@pytest.mark.parametrize("res,order,C,dtype", SHAPES)
+def test_binned_forward_backward_parity(tg, res, order, C, dtype):
+    coefs = W.init_coefs(3, res, order, C, seed=1, std=0.5)
+    g = tg.tg_create(3, res, order, C, dtype)
+    tg.tg_set_coefs(g, to_dev(coefs))
+    stored = tg.tg_get_coefs(g, which=0).cpu().numpy().astype(np.float64)
+    pts = np.concatenate([points(3, res, 20000, seed=2), clustered(2000)])
+    N = pts.shape[0]
+    P = to_dev(pts)
+    batch = tg.tg_batch_create(3, res, N)
+    tg.tg_batch_bin(batch, P)
+    out, gx = tg.tg_query_binned(g, batch, want_grad=True)
+    out_p, gx_p = tg.tg_query(g, P, want_grad=True)
+    r = np.random.default_rng(4)
+    dLdf = r.normal(size=(N, C)).astype(np.float32)
+    dLdg = r.normal(size=(N, C, 3)).astype(np.float32)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward_binned(g, batch, to_dev(dLdf), grad, dL_dgradx=to_dev(dLdg))
+    torch.cuda.synchronize()
+    assert tg.tg_batch_timeouts(batch) == 0
+    check_forward(out.cpu().numpy(), gx.cpu().numpy(), 3, res, order, C, stored, pts)
+    torch.testing.assert_close(out, out_p, rtol=1e-6, atol=1e-6)
+    torch.testing.assert_close(gx, gx_p, rtol=1e-5, atol=1e-5)
+    check_coef_grad(grad.cpu().numpy(), 3, res, order, C, pts, dLdf, dLdg)
+
+
+def test_binned_value_only_backward_and_rebin(tg):
+    res, order, C = 26, 2, 1
+    g = tg.tg_create(3, res, order, C, "f32", seed=3, init_std=0.3)
+    coefs = tg.tg_get_coefs(g, which=1).cpu().numpy()
+    batch = tg.tg_batch_create(3, res, 50000)
+    for seed, n in [(5, 50000), (6, 777), (7, 1)]:
+        pts = W.uniform_points(seed, n)
+        tg.tg_batch_bin(batch, to_dev(pts))
+        out = tg.tg_query_binned(g, batch)
+        dLdf = np.random.default_rng(seed).normal(size=(n, 1)).astype(np.float32)
+        grad = torch.zeros(g.n_coefs, device="cuda")
+        tg.tg_query_backward_binned(g, batch, to_dev(dLdf), grad)
+        torch.cuda.synchronize()
+        check_forward(out.cpu().numpy(), None, 3, res, order, C, coefs.astype(np.float64), pts)
+        check_coef_grad(grad.cpu().numpy(), 3, res, order, C, pts, dLdf)
+
+
+def test_binned_empty_batch(tg):
+    g = tg.tg_create(3, 10, 2, 1, "f32", init_std=0.1)
+    batch = tg.tg_batch_create(3, 10, 16)
+    tg.tg_batch_bin(batch, torch.empty((0, 3), device="cuda"))
+    out = tg.tg_query_binned(g, batch)
+    assert out.shape == (0, 1)
+
+
+def test_binned_rejects_unsupported(tg):
+    g = tg.tg_create(3, 11, 2, 1, "f32")          # 11 * 40 bytes is not a multiple of 16
+    batch = tg.tg_batch_create(3, 11, 16)
+    tg.tg_batch_bin(batch, torch.rand((16, 3), device="cuda"))
+    with pytest.raises(tg.TGError):
+        tg.tg_query_binned(g, batch)
+    with pytest.raises(tg.TGError):
+        tg.tg_batch_create(2, 10, 16)
+    with pytest.raises(tg.TGError):
+        tg.tg_batch_bin(batch, torch.rand((17, 3), device="cuda"))

@@ -1,0 +1,162 @@
+"""GPU parity of the query path (Eq. 2 - Eq. 4), its coefficient gradient and
+Adam against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from parity import check_coef_grad, check_forward, points, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [  # dim, res, order, C
+    (3, 5, 0, 1), (3, 9, 1, 1), (3, 12, 2, 1), (3, 7, 2, 3), (3, 6, 1, 3), (3, 6, 2, 2), (3, 5, 0, 4),
+    (2, 11, 2, 1), (2, 9, 1, 2), (2, 6, 0, 3),
+]
+
+
+def make_grid(tg, dim, res, order, C, dtype="f32", std=0.5, seed=0):
+    coefs = W.init_coefs(dim, res, order, C, seed=seed, std=std)
+    g = tg.tg_create(dim, res, order, C, dtype)
+    tg.tg_set_coefs(g, to_dev(coefs))
+    return g, coefs
+
+
+@pytest.mark.parametrize("dim,res", [(3, 7), (3, 256), (2, 33), (3, 2)])
+def test_locate_bit_exact(tg, dim, res):
+    pts = points(dim, res, 20000, seed=5)
+    cells, t = tg.tg_locate(dim, res, to_dev(pts))
+    rc, rt = oracle.locate(dim, res, pts)
+    assert np.array_equal(cells.cpu().numpy(), rc)
+    assert np.array_equal(t.cpu().numpy().astype(np.float64), rt)
+
+
+@pytest.mark.parametrize("dim,res,order,C", SHAPES)
+def test_forward_parity(tg, dim, res, order, C):
+    g, coefs = make_grid(tg, dim, res, order, C)
+    pts = points(dim, res, 3000)
+    out, gx = tg.tg_query(g, to_dev(pts), want_grad=True)
+    torch.cuda.synchronize()
+    check_forward(out.cpu().numpy(), gx.cpu().numpy(), dim, res, order, C, coefs.astype(np.float64), pts)
+
+
+@pytest.mark.parametrize("dim,res,order,C", SHAPES)
+def test_backward_parity(tg, dim, res, order, C):
+    g, coefs = make_grid(tg, dim, res, order, C)
+    pts = points(dim, res, 3000)
+    N = pts.shape[0]
+    r = np.random.default_rng(7)
+    dLdf = r.normal(size=(N, C)).astype(np.float32)
+    dLdg = r.normal(size=(N, C, dim)).astype(np.float32)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward(g, to_dev(pts), to_dev(dLdf), grad)
+    torch.cuda.synchronize()
+    check_coef_grad(grad.cpu().numpy(), dim, res, order, C, pts, dLdf)
+    grad.zero_()
+    tg.tg_query_backward(g, to_dev(pts), to_dev(dLdf), grad, dL_dgradx=to_dev(dLdg))
+    torch.cuda.synchronize()
+    check_coef_grad(grad.cpu().numpy(), dim, res, order, C, pts, dLdf, dLdg)
+
+
+def test_backward_sorted_points_warp_aggregation(tg):
+    """Many points per cell in warp order exercises the match/shuffle combine."""
+    dim, res, order, C = 3, 6, 2, 1
+    g, _ = make_grid(tg, dim, res, order, C)
+    pts = W.uniform_points(9, 8192)
+    cells, _ = oracle.locate(dim, res, pts)
+    key = cells[:, 0] + res * (cells[:, 1] + res * cells[:, 2])
+    pts = pts[np.argsort(key, kind="stable")]
+    r = np.random.default_rng(8)
+    dLdf = r.normal(size=(pts.shape[0], 1)).astype(np.float32)
+    dLdg = r.normal(size=(pts.shape[0], 1, 3)).astype(np.float32)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward(g, to_dev(pts), to_dev(dLdf), grad, dL_dgradx=to_dev(dLdg))
+    torch.cuda.synchronize()
+    check_coef_grad(grad.cpu().numpy(), dim, res, order, C, pts, dLdf, dLdg)
+
+
+def test_backward_accumulates(tg):
+    dim, res, order, C = 3, 5, 2, 1
+    g, _ = make_grid(tg, dim, res, order, C)
+    pts = points(dim, res, 500)
+    dLdf = np.ones((pts.shape[0], 1), np.float32)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward(g, to_dev(pts), to_dev(dLdf), grad)
+    once = grad.clone()
+    tg.tg_query_backward(g, to_dev(pts), to_dev(dLdf), grad)
+    torch.testing.assert_close(grad, 2 * once, rtol=1e-5, atol=1e-6)
+
+
+def test_empty_and_single_point(tg):
+    g, coefs = make_grid(tg, 3, 4, 2, 1)
+    empty = torch.empty((0, 3), device="cuda")
+    out = tg.tg_query(g, empty)
+    assert out.shape == (0, 1)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward(g, empty, torch.empty((0, 1), device="cuda"), grad)
+    assert not grad.any()
+    p = np.array([[0.3, 0.6, 0.9]], np.float32)
+    out = tg.tg_query(g, to_dev(p))
+    torch.cuda.synchronize()
+    check_forward(out.cpu().numpy(), None, 3, 4, 2, 1, coefs.astype(np.float64), p)
+
+
+def test_invalid_arguments_raise(tg):
+    with pytest.raises(tg.TGError):
+        tg.tg_create(3, 1, 2, 1)
+    with pytest.raises(tg.TGError):
+        tg.tg_create(3, 8, 5, 1)
+    g, _ = make_grid(tg, 3, 4, 1, 1)
+    with pytest.raises(ValueError):
+        tg.tg_query(g, torch.zeros((4, 3)))            # host tensor: no CPU path
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_low_precision_storage(tg, dtype, order):
+    """(i) against the oracle on the dequantised coefficients: FP32-level error;
+    (ii) against the oracle on the FP32 master: within 1e-2 relative."""
+    dim, res, C = 3, 10, 1
+    g, coefs = make_grid(tg, dim, res, order, C, dtype=dtype)
+    stored = tg.tg_get_coefs(g, which=0).cpu().numpy().astype(np.float64)
+    master = tg.tg_get_coefs(g, which=1).cpu().numpy()
+    assert np.array_equal(master, coefs)
+    pts = points(dim, res, 3000)
+    out, gx = tg.tg_query(g, to_dev(pts), want_grad=True)
+    torch.cuda.synchronize()
+    check_forward(out.cpu().numpy(), gx.cpu().numpy(), dim, res, order, C, stored, pts)
+    ref, _, _, _ = oracle.query(dim, res, order, C, coefs.astype(np.float64), pts, want_grad=False)
+    S = oracle.query_absscale(dim, res, order, C, coefs.astype(np.float64), pts)
+    assert (np.abs(out.cpu().numpy() - ref) <= 1e-2 * np.maximum(np.abs(ref), S)).all()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_adam_parity(tg, dtype):
+    dim, res, order, C = 3, 8, 2, 1
+    g, coefs = make_grid(tg, dim, res, order, C, dtype=dtype)
+    n = g.n_coefs
+    p = coefs.astype(np.float64).copy(); m = np.zeros(n); v = np.zeros(n)
+    r = np.random.default_rng(11)
+    grad = torch.zeros(n, device="cuda")
+    for step in range(1, 6):
+        gnp = r.normal(size=n).astype(np.float32) * (10.0 ** r.uniform(-3, 1, size=n)).astype(np.float32)
+        grad.copy_(to_dev(gnp))
+        tg.tg_adam_step(g, grad, lr=1e-2, step=step)
+        gg = gnp.astype(np.float64)
+        oracle.adam(p, gg, m, v, 1e-2, 0.9, 0.999, 1e-8, step)
+        torch.cuda.synchronize()
+        assert not grad.any()
+        got = tg.tg_get_coefs(g, which=1).cpu().numpy()
+        np.testing.assert_allclose(got, p, rtol=0, atol=2e-6 * step * 1e-2 * 10 + 1e-6 * np.abs(p).max())
+    stored = tg.tg_get_coefs(g, which=0).cpu().numpy()
+    master = tg.tg_get_coefs(g, which=1).cpu()
+    want = master.to(torch.bfloat16 if dtype == "bf16" else torch.float16 if dtype == "f16" else torch.float32)
+    assert np.array_equal(stored, want.float().numpy())
+
+
+def test_init_matches_generator(tg):
+    g = tg.tg_create(3, 6, 2, 1, "f32", seed=42, init_std=0.01)
+    got = tg.tg_get_coefs(g, which=1).cpu().numpy()
+    want = W.init_coefs(3, 6, 2, 1, seed=42, std=0.01)
+    np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-9)

@@ -1,0 +1,72 @@
+"""CPU-side checks: the library builds, loads and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*TG_API\s+(?:const\s+)?[a-z_0-9]+\s*\*?\s*(tg_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2402_14415_gb300.builder import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["tg_create", "tg_destroy", "tg_query", "tg_query_backward", "tg_adam_step", "tg_locate",
+                 "tg_batch_bin", "tg_query_binned", "tg_query_backward_binned"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_2402_14415_gb300 import binding
+    assert set(binding.exported_symbols()) <= set(declared_functions())
+
+
+def test_status_strings(lib):
+    lib.tg_status_string.restype = ctypes.c_char_p
+    assert lib.tg_status_string(0) == b"TG_OK"
+    assert lib.tg_status_string(3) == b"TG_EBUDGET"
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu(lib):
+    """Argument checks run on the host before any device call."""
+    h = ctypes.c_void_p()
+    lib.tg_create.argtypes = [ctypes.c_int] * 5 + [ctypes.c_uint64, ctypes.c_float, ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.tg_create(4, 8, 2, 1, 0, 0, 0.0, ctypes.byref(h)) == 1      # dim
+    assert lib.tg_create(3, 8, 3, 1, 0, 0, 0.0, ctypes.byref(h)) == 1      # order
+    assert lib.tg_create(3, 1, 2, 1, 0, 0, 0.0, ctypes.byref(h)) == 1      # res
+    assert lib.tg_create(3, 8, 2, 5, 0, 0, 0.0, ctypes.byref(h)) == 1      # channels
+    assert lib.tg_create(3, 8, 2, 1, 7, 0, 0.0, ctypes.byref(h)) == 1      # dtype
+    lib.tg_query.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p]
+    assert lib.tg_query(None, None, 0, None, None, None) == 1
+
+
+def test_product_path_has_no_oracle_reference():
+    """The package and the CUDA sources never import or link the oracle."""
+    pkg = os.path.join(ROOT, "paper_2402_14415_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "tg_oracle" not in txt, f
