@@ -1,0 +1,376 @@
+// Binning of a point batch by 8^3-cell brick (counting sort), and the batch API.
+//
+// With at most 32768 bricks each of G chunk blocks builds a shared-memory
+// histogram of its slice of the points, a column scan over the chunks turns
+// the histograms into per-chunk write cursors, and the place pass writes every
+// point once into brick order using shared-memory atomics only. Larger grids
+// fall back to global-atomic counting.
+#include <stdlib.h>
+
+#include <mutex>
+
+#include "tg_binned.cuh"
+
+namespace tg {
+
+constexpr int kBinThreads = 256;
+constexpr int kHistThreads = 1024;
+constexpr int kMaxSmemBins = 32768;   // 128 KB of shared counters
+constexpr int kColScanBricks = 32;    // bricks per block of the chunk-column scan
+
+__device__ __forceinline__ void load_point3(const float *__restrict__ pts, int64_t n, float *x)
+{
+    x[0] = __ldg(pts + 3 * n);
+    x[1] = __ldg(pts + 3 * n + 1);
+    x[2] = __ldg(pts + 3 * n + 2);
+}
+
+__global__ void __launch_bounds__(kHistThreads)
+bin_hist_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk, int res, int nbx, int nby, int nbricks,
+                int *__restrict__ hist)
+{
+    extern __shared__ int sh[];
+    for (int j = threadIdx.x; j < nbricks; j += blockDim.x) sh[j] = 0;
+    __syncthreads();
+    const float scale = (float)(res - 1);
+    const int64_t lo = (int64_t)blockIdx.x * chunk;
+    const int64_t hi = min(N, lo + chunk);
+    for (int64_t n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+        float x[3], t[3];
+        int c[3];
+        load_point3(pts, n, x);
+        locate<3>(x, res, scale, c, t);
+        atomicAdd(sh + brick_of(c, nbx, nby), 1);
+    }
+    __syncthreads();
+    int *dst = hist + (int64_t)blockIdx.x * nbricks;
+    for (int j = threadIdx.x; j < nbricks; j += blockDim.x) dst[j] = sh[j];
+}
+
+// Block-wide exclusive scan of one int per thread; returns this thread's
+// exclusive prefix and the block total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tmp, int &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_tmp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < nw ? warp_tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        warp_tmp[lane] = w;
+    }
+    __syncthreads();
+    total = warp_tmp[nw - 1];
+    const int excl = incl - v + (wid > 0 ? warp_tmp[wid - 1] : 0);
+    __syncthreads();
+    return excl;
+}
+
+// Column scan: for kColScanBricks bricks per block, the exclusive scan over
+// the G chunk histograms (in place, through shared memory so that every
+// global access is a coalesced row segment) and the brick totals.
+__global__ void __launch_bounds__(1024)
+bin_chunk_scan_kernel(int *__restrict__ hist, int G, int nbricks, int *__restrict__ totals)
+{
+    extern __shared__ int tile[];          // G x kColScanBricks
+    const int b0 = blockIdx.x * kColScanBricks;
+    const int nb = min(kColScanBricks, nbricks - b0);
+    for (int j = threadIdx.x; j < G * kColScanBricks; j += blockDim.x) {
+        const int g = j / kColScanBricks, c = j % kColScanBricks;
+        tile[j] = c < nb ? hist[(int64_t)g * nbricks + b0 + c] : 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = wid; c < nb; c += blockDim.x >> 5) {   // one warp per brick column
+        int carry = 0;
+        for (int g0 = 0; g0 < G; g0 += 32) {
+            const int g = g0 + lane;
+            const int v = g < G ? tile[g * kColScanBricks + c] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (g < G) tile[g * kColScanBricks + c] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) totals[b0 + c] = carry;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < G * kColScanBricks; j += blockDim.x) {
+        const int g = j / kColScanBricks, c = j % kColScanBricks;
+        if (c < nb) hist[(int64_t)g * nbricks + b0 + c] = tile[j];
+    }
+}
+
+// Single-block exclusive scan of counts[0..n) into offsets[0..n] (offsets[n] =
+// total) and optionally cursor; each thread owns a contiguous run per tile.
+__global__ void __launch_bounds__(1024)
+bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int *__restrict__ cursor, int n)
+{
+    __shared__ int warp_tmp[32];
+    constexpr int PER = 16;
+    int carry = 0;
+    const int per_tile = PER * blockDim.x;
+    for (int base = 0; base < n; base += per_tile) {
+        const int j0 = base + PER * threadIdx.x;
+        int v[PER];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            v[k] = (j0 + k < n) ? counts[j0 + k] : 0;
+            sum += v[k];
+        }
+        int total;
+        int run = carry + block_exclusive_scan(sum, warp_tmp, total);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (j0 + k < n) {
+                offsets[j0 + k] = run;
+                if (cursor) cursor[j0 + k] = run;
+            }
+            run += v[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) offsets[n] = carry;
+}
+
+__global__ void __launch_bounds__(kHistThreads)
+bin_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk, int res, int nbx, int nby, int nbricks,
+                 const int *__restrict__ hist, const int *__restrict__ offsets, float4 *__restrict__ sorted)
+{
+    extern __shared__ int cur[];
+    const int *h = hist + (int64_t)blockIdx.x * nbricks;
+    for (int j = threadIdx.x; j < nbricks; j += blockDim.x) cur[j] = __ldg(offsets + j) + __ldg(h + j);
+    __syncthreads();
+    const float scale = (float)(res - 1);
+    const int64_t lo = (int64_t)blockIdx.x * chunk;
+    const int64_t hi = min(N, lo + chunk);
+    constexpr int U = 4;   // points in flight per thread
+    for (int64_t n0 = lo + threadIdx.x; n0 < hi; n0 += (int64_t)U * blockDim.x) {
+        float x[U][3];
+        int slot[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t n = n0 + (int64_t)u * blockDim.x;
+            if (n < hi) load_point3(pts, n, x[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t n = n0 + (int64_t)u * blockDim.x;
+            if (n < hi) {
+                int c[3];
+                float t[3];
+                locate<3>(x[u], res, scale, c, t);
+                slot[u] = atomicAdd(cur + brick_of(c, nbx, nby), 1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t n = n0 + (int64_t)u * blockDim.x;
+            if (n < hi) sorted[slot[u]] = make_float4(x[u][0], x[u][1], x[u][2], __int_as_float((int)n));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+bin_count_kernel(const float *__restrict__ pts, int64_t N, int res, int nbx, int nby, int *__restrict__ counts)
+{
+    const float scale = (float)(res - 1);
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        float x[3], t[3];
+        int c[3];
+        load_point3(pts, n, x);
+        locate<3>(x, res, scale, c, t);
+        atomicAdd(counts + brick_of(c, nbx, nby), 1);
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+bin_scatter_kernel(const float *__restrict__ pts, int64_t N, int res, int nbx, int nby, int *__restrict__ cursor,
+                   float4 *__restrict__ sorted)
+{
+    const float scale = (float)(res - 1);
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        float x[3], t[3];
+        int c[3];
+        load_point3(pts, n, x);
+        locate<3>(x, res, scale, c, t);
+        const int slot = atomicAdd(cursor + brick_of(c, nbx, nby), 1);
+        sorted[slot] = make_float4(x[0], x[1], x[2], __int_as_float((int)n));
+    }
+}
+
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+tg_status make_brick_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem, int res, int nv,
+                         int box_z)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(TG_EDEVICE, "cuTensorMapEncodeTiled is unavailable from the driver");
+    const int bxi = box_inner_host(nv, elem);
+    if (bxi > 256) return fail(TG_EINVAL, "binned path: a brick row of %d elements exceeds the TMA box limit", bxi);
+    if (((size_t)res * nv * elem) % 16 != 0)
+        return fail(TG_EINVAL, "binned path: res * K * channels * elem (%d * %d * %d) must be a multiple of 16 bytes",
+                    res, nv, elem);
+    if (((uintptr_t)base & 15) != 0) return fail(TG_EINVAL, "binned path: array must be 16-byte aligned");
+    cuuint64_t dims[3] = {(cuuint64_t)res * nv, (cuuint64_t)res, (cuuint64_t)res};
+    cuuint64_t strides[2] = {(cuuint64_t)res * nv * elem, (cuuint64_t)res * res * nv * elem};
+    cuuint32_t box[3] = {(cuuint32_t)bxi, (cuuint32_t)kBV, (cuuint32_t)box_z};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, dt, 3, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(TG_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TG_OK;
+}
+
+tg_status set_smem(const void *kernel, int bytes)
+{
+    if (bytes <= 48 * 1024) return TG_OK;
+    return cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+                       "binned path: shared memory attribute");
+}
+
+tg_status check_pair(const tg_grid *g, const tg_batch *bt, const char *who)
+{
+    if (!g || !bt) return fail(TG_EINVAL, "%s: NULL grid or batch", who);
+    if (g->dim != 3 || bt->res != g->res) return fail(TG_EINVAL, "%s: batch was created for another grid shape", who);
+    return TG_OK;
+}
+
+static unsigned grid_for(const void *kernel, int threads, int64_t N)
+{
+    int64_t need = (N + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms() * blocks_per_sm(kernel, threads, 0);
+    return (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
+}  // namespace tg
+
+using namespace tg;
+
+extern "C" {
+
+tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
+{
+    if (!out) return fail(TG_EINVAL, "tg_batch_create: out is NULL");
+    *out = nullptr;
+    if (dim != 3) return fail(TG_EINVAL, "tg_batch_create: the binned path is 3-D only");
+    if (res < 2 || res > 2048) return fail(TG_EINVAL, "tg_batch_create: res %d out of range", res);
+    if (max_points < 0 || max_points > (int64_t)INT32_MAX) return fail(TG_EINVAL, "tg_batch_create: max_points out of range");
+    tg_batch *b = (tg_batch *)calloc(1, sizeof(tg_batch));
+    if (!b) return fail(TG_ENOMEM, "tg_batch_create: host allocation failed");
+    b->dim = dim; b->res = res; b->max_points = max_points;
+    cudaGetDevice(&b->device);
+    b->nbricks = 1;
+    for (int d = 0; d < 3; ++d) {
+        b->nb[d] = (res - 1 + kBrick - 1) / kBrick;
+        b->nbricks *= b->nb[d];
+    }
+    b->G = b->nbricks <= kMaxSmemBins ? num_sms() : 0;
+    tg_status st = cuda_status(cudaMalloc(&b->counts, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->offsets, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->cursor, b->nbricks * sizeof(int)), "tg_batch_create");
+    if (st == TG_OK && b->G)
+        st = cuda_status(cudaMalloc(&b->hist, (size_t)b->G * b->nbricks * sizeof(int)), "tg_batch_create");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->sorted, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->status, sizeof(int)), "tg_batch_create");
+    if (st == TG_OK) st = cuda_status(cudaMemset(b->offsets, 0, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
+    if (st == TG_OK) st = cuda_status(cudaMemset(b->status, 0, sizeof(int)), "tg_batch_create");
+    if (st == TG_OK && b->G) {
+        const int bytes = (int)(b->nbricks * sizeof(int));
+        st = set_smem((const void *)bin_hist_kernel, bytes);
+        if (st == TG_OK) st = set_smem((const void *)bin_place_kernel, bytes);
+        if (st == TG_OK) st = set_smem((const void *)bin_chunk_scan_kernel, b->G * kColScanBricks * (int)sizeof(int));
+    }
+    if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_batch_create");
+    if (st != TG_OK) { tg_batch_destroy(b); return st; }
+    *out = b;
+    return TG_OK;
+}
+
+tg_status tg_batch_destroy(tg_batch *b)
+{
+    if (!b) return TG_OK;
+    cudaFree(b->counts); cudaFree(b->offsets); cudaFree(b->cursor); cudaFree(b->hist); cudaFree(b->sorted);
+    cudaFree(b->status);
+    free(b);
+    return TG_OK;
+}
+
+tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream stream)
+{
+    if (!b) return fail(TG_EINVAL, "tg_batch_bin: batch is NULL");
+    if (N < 0 || N > b->max_points) return fail(TG_EINVAL, "tg_batch_bin: N=%lld outside [0, %lld]", (long long)N, (long long)b->max_points);
+    if (N > 0 && !pts) return fail(TG_EINVAL, "tg_batch_bin: pts is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    b->n = N;
+    const int nbx = b->nb[0], nby = b->nb[1];
+    const int nbr = (int)b->nbricks;
+    tg_status st;
+    if (N == 0) return cuda_status(cudaMemsetAsync(b->offsets, 0, (b->nbricks + 1) * sizeof(int), s), "tg_batch_bin");
+    if (b->G) {
+        const int64_t chunk = (N + b->G - 1) / b->G;
+        const int smem = nbr * (int)sizeof(int);
+        bin_hist_kernel<<<b->G, kHistThreads, smem, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist);
+        if ((st = launch_status("tg_batch_bin: histogram")) != TG_OK) return st;
+        bin_chunk_scan_kernel<<<(nbr + kColScanBricks - 1) / kColScanBricks, 1024,
+                                b->G * kColScanBricks * sizeof(int), s>>>(b->hist, b->G, nbr, b->counts);
+        if ((st = launch_status("tg_batch_bin: chunk scan")) != TG_OK) return st;
+        bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, nullptr, nbr);
+        if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;
+        bin_place_kernel<<<b->G, kHistThreads, smem, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist, b->offsets,
+                                                          b->sorted);
+        return launch_status("tg_batch_bin: place");
+    }
+    if ((st = cuda_status(cudaMemsetAsync(b->counts, 0, (b->nbricks + 1) * sizeof(int), s), "tg_batch_bin")) != TG_OK)
+        return st;
+    bin_count_kernel<<<grid_for((const void *)bin_count_kernel, kBinThreads, N), kBinThreads, 0, s>>>(
+        pts, N, b->res, nbx, nby, b->counts);
+    if ((st = launch_status("tg_batch_bin: count")) != TG_OK) return st;
+    bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, b->cursor, nbr);
+    if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;
+    bin_scatter_kernel<<<grid_for((const void *)bin_scatter_kernel, kBinThreads, N), kBinThreads, 0, s>>>(
+        pts, N, b->res, nbx, nby, b->cursor, b->sorted);
+    return launch_status("tg_batch_bin: scatter");
+}
+
+tg_status tg_batch_timeouts(tg_batch *b, int *timed_out)
+{
+    if (!b || !timed_out) return fail(TG_EINVAL, "tg_batch_timeouts: NULL argument");
+    int v = 0;
+    tg_status st = cuda_status(cudaMemcpy(&v, b->status, sizeof(int), cudaMemcpyDeviceToHost), "tg_batch_timeouts");
+    if (st != TG_OK) return st;
+    *timed_out = v;
+    if (v) cudaMemset(b->status, 0, sizeof(int));
+    return TG_OK;
+}
+
+}  // extern "C"

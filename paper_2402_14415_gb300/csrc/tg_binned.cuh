@@ -1,0 +1,56 @@
+// Shared definitions of the brick-binned query path (3-D).
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include "tg_internal.cuh"
+#include "tg_tma.cuh"
+
+struct tg_batch {
+    int dim, res;
+    int nb[3];            // bricks per axis
+    int64_t nbricks;
+    int64_t max_points;
+    int64_t n;            // points binned by the last tg_batch_bin
+    int G;                // chunk blocks of the histogram binning (0: global-atomic binning)
+    int *counts;          // nbricks + 1 (global-atomic binning) / per-brick totals
+    int *offsets;         // nbricks + 1, exclusive prefix sum of the brick counts
+    int *cursor;          // nbricks, scatter cursors (global-atomic binning)
+    int *hist;            // G x nbricks chunk histograms, then chunk cursors
+    float4 *sorted;       // max_points: (x, y, z, original index as int bits)
+    int *status;          // device word: non-zero after a bounded wait gave up
+    int device;
+};
+
+namespace tg {
+
+constexpr int kBrick = 8;                              // cells per brick edge
+constexpr int kBV = kBrick + 1;                        // vertices per brick edge
+constexpr int kBrickCells = kBrick * kBrick * kBrick;  // 512
+
+// Elements per brick row in a TMA box: the 9 vertex blocks padded to 16 bytes.
+template <typename T, int NV>
+struct BoxInner {
+    static constexpr int bytes = (kBV * NV * (int)sizeof(T) + 15) / 16 * 16;
+    static constexpr int value = bytes / (int)sizeof(T);
+    static constexpr int tile_bytes = kBV * kBV * bytes;   // a full 9 x 9 x 9 brick
+};
+
+inline int box_inner_host(int nv, int elem) { return ((kBV * nv * elem + 15) / 16 * 16) / elem; }
+
+__device__ __forceinline__ int brick_of(const int *c, int nbx, int nby)
+{
+    return (c[0] / kBrick) + nbx * ((c[1] / kBrick) + nby * (c[2] / kBrick));
+}
+
+// Tensor map of a res^3 x nv array (coefficients or gradient) viewed as the
+// 3-D tensor [z][y][x * nv], with a box of box_z planes of 9 brick rows.
+tg_status make_brick_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem, int res, int nv,
+                         int box_z);
+
+// Opts a kernel in to more than 48 KB of dynamic shared memory.
+tg_status set_smem(const void *kernel, int bytes);
+
+tg_status check_pair(const tg_grid *g, const tg_batch *bt, const char *who);
+
+}  // namespace tg

@@ -1,0 +1,173 @@
+// Brick-binned forward query (Eq. 2 - Eq. 4): one block per 8^3-cell brick
+// TMA-loads the brick's 9^3 vertex blocks into shared memory with one 3-D
+// tiled copy, then evaluates its points from there using per-point delta
+// tables (one FMA per coefficient and corner).
+#include "tg_binned.cuh"
+
+namespace tg {
+
+constexpr int kFwdThreads = 256;
+
+template <typename T, int NV>
+__device__ __forceinline__ void load_block_smem(const T *p, float *out)
+{
+    constexpr int BYTES = NV * (int)sizeof(T);
+    constexpr int VW = VecWidth<BYTES>::value;
+    constexpr int NW = BYTES / VW;
+    if constexpr (VW == 16) {
+        uint4 r[NW];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r[i] = reinterpret_cast<const uint4 *>(p)[i];
+        const T *tp = reinterpret_cast<const T *>(r);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] = to_f32<T>(tp[j]);
+    } else if constexpr (VW == 8) {
+        uint2 r[NW];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r[i] = reinterpret_cast<const uint2 *>(p)[i];
+        const T *tp = reinterpret_cast<const T *>(r);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] = to_f32<T>(tp[j]);
+    } else if constexpr (VW == 4) {
+        unsigned r[NW];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) r[i] = reinterpret_cast<const unsigned *>(p)[i];
+        const T *tp = reinterpret_cast<const T *>(r);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] = to_f32<T>(tp[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] = to_f32<T>(p[j]);
+    }
+}
+
+template <typename T, int ORDER, int C, bool WANT_GRAD>
+__global__ void __launch_bounds__(kFwdThreads)
+brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int nby,
+                 const float4 *__restrict__ sorted, const int *__restrict__ offsets, float *__restrict__ out,
+                 float *__restrict__ gx, int *__restrict__ status)
+{
+    constexpr int K = Basis<3, ORDER>::K;
+    constexpr int NV = K * C;
+    constexpr int BXI = BoxInner<T, NV>::value;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    uint64_t &bar = *reinterpret_cast<uint64_t *>(smem_raw + BoxInner<T, NV>::tile_bytes);
+
+    const int b = blockIdx.x;
+    const int p0 = offsets[b], p1 = offsets[b + 1];
+    if (p0 == p1) return;
+    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+    const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, BoxInner<T, NV>::tile_bytes);
+        tma_load_3d(tile, &cmap, x0 * NV, y0, z0, &bar);
+    }
+    if (!mbar_wait_bounded(&bar, 0)) {
+        if (threadIdx.x == 0) atomicExch(status, 1);
+        mbar_wait_bounded(&bar, 0);          // second bounded wait for the copy in flight
+        return;
+    }
+
+    const float scale = (float)(res - 1);
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const float4 q = sorted[p];
+        const int64_t n = __float_as_int(q.w);
+        const float x[3] = {q.x, q.y, q.z};
+        int c[3];
+        float t[3];
+        locate<3>(x, res, scale, c, t);
+        const PointTables3<ORDER> P(t);
+        const T *cell = tile + ((c[2] - z0) * kBV + (c[1] - y0)) * BXI + (c[0] - x0) * NV;
+        float f[C], gu[C][3];
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) {
+            f[ch] = 0.f;
+            gu[ch][0] = gu[ch][1] = gu[ch][2] = 0.f;
+        }
+        for_corners<0>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            constexpr int off = ((I >> 2) & 1) * kBV * BXI + ((I >> 1) & 1) * BXI + (I & 1) * NV;
+            float th[NV];
+            load_block_smem<T, NV>(cell + off, th);
+            const float w = P.template weight<I>();
+            float dw[3];
+            if constexpr (WANT_GRAD) P.template dweight<I>(dw);
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) {
+                const float Tv = P.template value<I>(th + ch * K);       // Eq. 3
+                f[ch] = fmaf(w, Tv, f[ch]);                               // Eq. 4
+                if constexpr (WANT_GRAD) {
+                    float g[3];
+                    P.template gradient<I>(th + ch * K, g);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) gu[ch][d] = fmaf(dw[d], Tv, fmaf(w, g[d], gu[ch][d]));
+                }
+            }
+        });
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) {
+            out[n * C + ch] = f[ch];
+            if constexpr (WANT_GRAD) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) gx[(n * C + ch) * 3 + d] = gu[ch][d] * scale;
+            }
+        }
+    }
+}
+
+template <typename T>
+struct BinnedFwd {
+    template <int DIM, int ORDER, int C>
+    static tg_status run(const tg_grid *g, const tg_batch *bt, float *out, float *gx, cudaStream_t s)
+    {
+        if constexpr (DIM != 3) {
+            return fail(TG_EINVAL, "binned path is 3-D only");
+        } else {
+            constexpr int NV = Basis<3, ORDER>::K * C;
+            CUtensorMap map;
+            const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : (g->dtype == TG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+            tg_status st = make_brick_map(&map, g->store, dt, (int)sizeof(T), g->res, NV, kBV);
+            if (st != TG_OK) return st;
+            const int smem = BoxInner<T, NV>::tile_bytes + 16;     // tile + mbarrier
+            if (gx) {
+                auto k = brick_fwd_kernel<T, ORDER, C, true>;
+                if ((st = set_smem((const void *)k, smem)) != TG_OK) return st;
+                k<<<(unsigned)bt->nbricks, kFwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
+                                                                   bt->offsets, out, gx, bt->status);
+            } else {
+                auto k = brick_fwd_kernel<T, ORDER, C, false>;
+                if ((st = set_smem((const void *)k, smem)) != TG_OK) return st;
+                k<<<(unsigned)bt->nbricks, kFwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
+                                                                   bt->offsets, out, nullptr, bt->status);
+            }
+            return launch_status("tg_query_binned");
+        }
+    }
+};
+
+}  // namespace tg
+
+using namespace tg;
+
+extern "C" tg_status tg_query_binned(const tg_grid *g, const tg_batch *bt, float *out, float *grad_x, tg_stream stream)
+{
+    tg_status st = check_pair(g, bt, "tg_query_binned");
+    if (st != TG_OK) return st;
+    if (bt->n == 0) return TG_OK;
+    if (!out) return fail(TG_EINVAL, "tg_query_binned: out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+#define TG_QB(D, O, C)                                                                      \
+    (g->dtype == TG_F32    ? BinnedFwd<float>::run<D, O, C>(g, bt, out, grad_x, s)          \
+     : g->dtype == TG_BF16 ? BinnedFwd<__nv_bfloat16>::run<D, O, C>(g, bt, out, grad_x, s)  \
+                           : BinnedFwd<__half>::run<D, O, C>(g, bt, out, grad_x, s))
+    return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_QB);
+#undef TG_QB
+}

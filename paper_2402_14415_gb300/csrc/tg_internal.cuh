@@ -6,6 +6,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/taylorgrid.h"
 
 struct tg_grid {
@@ -199,6 +201,39 @@ struct Basis {
         return T;
     }
 
+    // acc_k += s phi_k(delta) (+ sum_d q_d dphi_k/ddelta_d when HAS_Q).
+    template <bool HAS_Q>
+    __device__ __forceinline__ static void accumulate(float s, const float *q, const float *dl, float *acc)
+    {
+        acc[0] += s;
+        if constexpr (ORDER >= 1) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) acc[1 + d] = fmaf(s, dl[d], HAS_Q ? acc[1 + d] + q[d] : acc[1 + d]);
+        }
+        if constexpr (ORDER >= 2) {
+            float hs = 0.5f * s;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                float a = fmaf(hs, dl[d] * dl[d], acc[1 + DIM + d]);
+                acc[1 + DIM + d] = HAS_Q ? fmaf(q[d], dl[d], a) : a;
+            }
+            if constexpr (DIM == 3) {
+                const float sx = s * dl[0];
+                float a7 = fmaf(sx, dl[1], acc[7]), a8 = fmaf(sx, dl[2], acc[8]), a9 = fmaf(s * dl[1], dl[2], acc[9]);
+                if constexpr (HAS_Q) {
+                    a7 = fmaf(q[0], dl[1], fmaf(q[1], dl[0], a7));
+                    a8 = fmaf(q[0], dl[2], fmaf(q[2], dl[0], a8));
+                    a9 = fmaf(q[1], dl[2], fmaf(q[2], dl[1], a9));
+                }
+                acc[7] = a7; acc[8] = a8; acc[9] = a9;
+            } else {
+                float a5 = fmaf(s * dl[0], dl[1], acc[5]);
+                if constexpr (HAS_Q) a5 = fmaf(q[0], dl[1], fmaf(q[1], dl[0], a5));
+                acc[5] = a5;
+            }
+        }
+    }
+
     // Adjoint of eval: given s = dL/dT and q = dL/d(grad T), returns
     // dL/dtheta_k = s phi_k + sum_d q_d dphi_k/ddelta_d.
     __device__ __forceinline__ static void adjoint(float s, const float *q, const float *dl, float *out)
@@ -255,6 +290,145 @@ __device__ __forceinline__ int64_t corner_offset(int i, int res)
     if (i & 2) o += res;
     if (DIM == 3 && (i & 4)) o += (int64_t)res * res;
     return o;
+}
+
+// ---------------------------------------------------------------------------
+// 3-D point tables: everything of Eq. 3 / Eq. 4 that depends on the point
+// but not on the corner's coefficients, computed once per point. For corner
+// bits b, delta_d = u[b_d][d]; the series basis is
+//   1, u[b_d][d], h[b_d][d] = u^2 / 2, p_ab[b_a][b_b] = u[b_a][a] u[b_b][b]
+// and the blend weight is w = a[b_x][0] a[b_y][1] a[b_z][2], a[0] = 1 - t,
+// a[1] = t. T_i and its adjoint then cost one FMA per coefficient.
+// ---------------------------------------------------------------------------
+template <int ORDER>
+struct PointTables3 {
+    float u[2][3];            // delta components t - b
+    float h[2][3];            // delta^2 / 2
+    float pxy[2][2], pxz[2][2], pyz[2][2];
+    float a[2][3];            // weight factors
+    float wxy[2][2];          // a_x a_y
+
+    __device__ __forceinline__ explicit PointTables3(const float *t)
+    {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            u[0][d] = t[d];
+            u[1][d] = t[d] - 1.0f;
+            a[0][d] = 1.0f - t[d];
+            a[1][d] = t[d];
+            if (ORDER >= 2) {
+                h[0][d] = 0.5f * u[0][d] * u[0][d];
+                h[1][d] = 0.5f * u[1][d] * u[1][d];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                wxy[i][j] = a[i][0] * a[j][1];
+                if (ORDER >= 2) {
+                    pxy[i][j] = u[i][0] * u[j][1];
+                    pxz[i][j] = u[i][0] * u[j][2];
+                    pyz[i][j] = u[i][1] * u[j][2];
+                }
+            }
+    }
+
+    template <int I>
+    __device__ __forceinline__ float weight() const
+    {
+        return wxy[I & 1][(I >> 1) & 1] * a[(I >> 2) & 1][2];
+    }
+
+    // d w / d t_d for corner I.
+    template <int I>
+    __device__ __forceinline__ void dweight(float *dw) const
+    {
+        constexpr int bx = I & 1, by = (I >> 1) & 1, bz = (I >> 2) & 1;
+        dw[0] = (bx ? 1.f : -1.f) * a[by][1] * a[bz][2];
+        dw[1] = (by ? 1.f : -1.f) * a[bx][0] * a[bz][2];
+        dw[2] = (bz ? 1.f : -1.f) * wxy[bx][by];
+    }
+
+    // T_i = sum_k theta_k phi_k(delta_i) (Eq. 1 / Eq. 3).
+    template <int I>
+    __device__ __forceinline__ float value(const float *th) const
+    {
+        constexpr int bx = I & 1, by = (I >> 1) & 1, bz = (I >> 2) & 1;
+        float T = th[0];
+        if constexpr (ORDER >= 1) {
+            T = fmaf(th[1], u[bx][0], T);
+            T = fmaf(th[2], u[by][1], T);
+            T = fmaf(th[3], u[bz][2], T);
+        }
+        if constexpr (ORDER >= 2) {
+            T = fmaf(th[4], h[bx][0], T);
+            T = fmaf(th[5], h[by][1], T);
+            T = fmaf(th[6], h[bz][2], T);
+            T = fmaf(th[7], pxy[bx][by], T);
+            T = fmaf(th[8], pxz[bx][bz], T);
+            T = fmaf(th[9], pyz[by][bz], T);
+        }
+        return T;
+    }
+
+    // d T_i / d delta = g + H delta.
+    template <int I>
+    __device__ __forceinline__ void gradient(const float *th, float *g) const
+    {
+        constexpr int bx = I & 1, by = (I >> 1) & 1, bz = (I >> 2) & 1;
+        if constexpr (ORDER == 0) {
+            g[0] = g[1] = g[2] = 0.f;
+        } else {
+            g[0] = th[1]; g[1] = th[2]; g[2] = th[3];
+            if constexpr (ORDER >= 2) {
+                const float ux = u[bx][0], uy = u[by][1], uz = u[bz][2];
+                g[0] = fmaf(th[4], ux, fmaf(th[7], uy, fmaf(th[8], uz, g[0])));
+                g[1] = fmaf(th[5], uy, fmaf(th[7], ux, fmaf(th[9], uz, g[1])));
+                g[2] = fmaf(th[6], uz, fmaf(th[8], ux, fmaf(th[9], uy, g[2])));
+            }
+        }
+    }
+
+    // acc_k += s phi_k(delta_i) (+ sum_d q_d d phi_k / d delta_d when HAS_Q).
+    template <int I, bool HAS_Q>
+    __device__ __forceinline__ void accumulate(float s, const float *q, float *acc) const
+    {
+        constexpr int bx = I & 1, by = (I >> 1) & 1, bz = (I >> 2) & 1;
+        acc[0] += s;
+        if constexpr (ORDER >= 1) {
+            const float ux = u[bx][0], uy = u[by][1], uz = u[bz][2];
+            acc[1] = fmaf(s, ux, HAS_Q ? acc[1] + q[0] : acc[1]);
+            acc[2] = fmaf(s, uy, HAS_Q ? acc[2] + q[1] : acc[2]);
+            acc[3] = fmaf(s, uz, HAS_Q ? acc[3] + q[2] : acc[3]);
+            if constexpr (ORDER >= 2) {
+                acc[4] = fmaf(s, h[bx][0], acc[4]);
+                acc[5] = fmaf(s, h[by][1], acc[5]);
+                acc[6] = fmaf(s, h[bz][2], acc[6]);
+                acc[7] = fmaf(s, pxy[bx][by], acc[7]);
+                acc[8] = fmaf(s, pxz[bx][bz], acc[8]);
+                acc[9] = fmaf(s, pyz[by][bz], acc[9]);
+                if constexpr (HAS_Q) {
+                    acc[4] = fmaf(q[0], ux, acc[4]);
+                    acc[5] = fmaf(q[1], uy, acc[5]);
+                    acc[6] = fmaf(q[2], uz, acc[6]);
+                    acc[7] = fmaf(q[0], uy, fmaf(q[1], ux, acc[7]));
+                    acc[8] = fmaf(q[0], uz, fmaf(q[2], ux, acc[8]));
+                    acc[9] = fmaf(q[1], uz, fmaf(q[2], uy, acc[9]));
+                }
+            }
+        }
+    }
+};
+
+// Compile-time loop over the 8 corners: F::template run<I>() for I = 0..7.
+template <int I, typename F>
+__device__ __forceinline__ void for_corners(F &&f)
+{
+    if constexpr (I < 8) {
+        f(std::integral_constant<int, I>{});
+        for_corners<I + 1>(f);
+    }
 }
 
 // Counter-based generator: splitmix64 (Steele, Lea & Flood 2014).
