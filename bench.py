@@ -304,6 +304,32 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def profile_once():
+    """One untimed pass of every kernel of the step (value and spatial-gradient variants)."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    tg.load()
+    n = int(sys.argv[sys.argv.index("--profile-points") + 1]) if "--profile-points" in sys.argv else N_POINTS
+    g = tg.tg_create(3, RES, ORDER, C, "f32", seed=0, init_std=1.0)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    P = torch.rand((n, 3), device="cuda", generator=gen)
+    U = torch.randn((n, 1), device="cuda", generator=gen)
+    UG = torch.randn((n, 1, 3), device="cuda", generator=gen)
+    out = torch.empty((n, 1), device="cuda")
+    gx = torch.empty((n, 1, 3), device="cuda")
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    batch = tg.tg_batch_create(3, RES, n)
+    tg.tg_batch_bin(batch, P)
+    tg.tg_query_binned(g, batch, out=out)
+    tg.tg_query_backward_binned(g, batch, U, grad)
+    tg.tg_query_binned(g, batch, out=out, grad_x=gx)
+    tg.tg_query_backward_binned(g, batch, U, grad, dL_dgradx=UG)
+    tg.tg_adam_step(g, grad, lr=1e-3, step=1)
+    torch.cuda.synchronize()
+    print("profile pass done, timeouts:", tg.tg_batch_timeouts(batch))
+
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture summarised in profiles/; None when the kernel changed since.
 TRAFFIC = {"forward": None, "backward": None, "bin": None}
@@ -316,8 +342,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="run each kernel of the step once, untimed (for ncu captures)")
+    ap.add_argument("--profile-points", type=int, default=N_POINTS)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile:
+        return profile_once()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)
