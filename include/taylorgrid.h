@@ -184,6 +184,26 @@ TG_API tg_status tg_query_backward_binned(const tg_grid *grid, const tg_batch *b
  * its outputs are invalid) and clears it. */
 TG_API tg_status tg_batch_timeouts(tg_batch *batch, int *timed_out);
 
+/* Binned forward query that allocates nothing (the paper has no counterpart;
+ * this is a deployment convenience). Some callers cannot call cudaMalloc:
+ * code embedded in a host framework that owns every device allocation, or a
+ * latency-critical serving path that must never reach the allocator. For
+ * them this call bins the N points (device, N x 3) and evaluates f (and, if
+ * grad_x is not NULL, the world-unit spatial gradient) exactly like
+ * tg_batch_bin + tg_query_binned, with all scratch held in one fixed array
+ * of about 4.4 MB compiled into the library (every GPU that loads the
+ * library keeps it until the process exits).
+ * Limits: N <= 262144 points and res <= 257 (at most 32768 bricks); larger
+ * requests fail with TG_EINVAL and a message. 3-D grids only, with the same
+ * shape rules as tg_query_binned.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Every call reuses the same array and leaves its contents behind (the call
+ * clears what must start at zero), so calls whose GPU work overlaps - on two
+ * streams, or from two threads - race and give wrong results: serialise them. */
+TG_API tg_status tg_query_noalloc(const tg_grid *grid, const float *pts, int64_t N,
+                                  float *out, float *grad_x, tg_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Optimiser. The paper fixes only the learning rate (Sec. 4.1, "fixed
  * learning rate of 0.003"); the engine uses Adam (Kingma & Ba 2015) with

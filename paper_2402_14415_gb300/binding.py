@@ -62,6 +62,7 @@ _SIGS = {
     "tg_query_binned": [_vp, _vp, _vp, _vp, _vp],
     "tg_query_backward_binned": [_vp, _vp, _vp, _vp, _vp, _vp],
     "tg_batch_timeouts": [_vp, ctypes.POINTER(_int)],
+    "tg_query_noalloc": [_vp, _vp, _i64, _vp, _vp, _vp],
     "tg_adam_step": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
 }
 
@@ -257,6 +258,20 @@ def tg_batch_timeouts(batch: Batch) -> int:
     v = _int(0)
     _check(load().tg_batch_timeouts(batch.handle, ctypes.byref(v)), "tg_batch_timeouts")
     return v.value
+
+
+def tg_query_noalloc(grid: Grid, pts: torch.Tensor, out=None, grad_x=None, want_grad=False, stream=None):
+    """Binned forward query served entirely from the library's fixed scratch array (no allocation)."""
+    N = pts.shape[0]
+    if out is None:
+        out = torch.empty((N, grid.channels), device=pts.device, dtype=torch.float32)
+    if grad_x is None and want_grad:
+        grad_x = torch.empty((N, grid.channels, grid.dim), device=pts.device, dtype=torch.float32)
+    _check(load().tg_query_noalloc(grid.handle, _ptr(pts, "pts", numel=N * grid.dim), N,
+                                   _ptr(out, "out", numel=N * grid.channels),
+                                   _ptr(grad_x, "grad_x", numel=N * grid.channels * grid.dim, optional=True),
+                                   _stream(stream)), "tg_query_noalloc")
+    return (out, grad_x) if (want_grad or grad_x is not None) else out
 
 
 def tg_adam_step(grid: Grid, coef_grad, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

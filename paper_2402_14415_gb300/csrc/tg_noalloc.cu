@@ -1,0 +1,89 @@
+// tg_query_noalloc: the brick-binned forward query for callers that cannot
+// allocate device memory. All of its scratch (brick counters, offsets, write
+// cursors, the sorted point records and a status word) lives in one
+// file-scope device array of fixed size; the call itself never allocates.
+#include <mutex>
+
+#include "tg_binned.cuh"
+
+namespace tg {
+
+constexpr int64_t kNoallocMaxPoints = (int64_t)1 << 18;     // 262144 points per call
+constexpr int64_t kNoallocMaxBricks = 32768;                // res <= 257
+
+struct NoallocScratch {
+    int counts[kNoallocMaxBricks + 1];
+    int offsets[kNoallocMaxBricks + 1];
+    int cursor[kNoallocMaxBricks];
+    int status[4];
+    float4 sorted[kNoallocMaxPoints];
+};
+
+// About 4.4 MB; every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
+
+// Device address of the scratch array, looked up once per device with that
+// device current (in host code the array's name is only a stand-in).
+static tg_status scratch_address(NoallocScratch **out)
+{
+    static std::mutex mu;
+    static void *addr[64] = {nullptr};
+    int dev = 0;
+    tg_status st = cuda_status(cudaGetDevice(&dev), "tg_query_noalloc: cudaGetDevice");
+    if (st != TG_OK) return st;
+    if (dev < 0 || dev >= 64) return fail(TG_EINVAL, "tg_query_noalloc: device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        st = cuda_status(cudaGetSymbolAddress(&p, g_noalloc_scratch), "tg_query_noalloc: cudaGetSymbolAddress");
+        if (st != TG_OK) return st;
+        addr[dev] = p;
+    }
+    *out = reinterpret_cast<NoallocScratch *>(addr[dev]);
+    return TG_OK;
+}
+
+}  // namespace tg
+
+using namespace tg;
+
+extern "C" tg_status tg_query_noalloc(const tg_grid *g, const float *pts, int64_t N, float *out, float *grad_x,
+                                      tg_stream stream)
+{
+    if (!g) return fail(TG_EINVAL, "tg_query_noalloc: grid is NULL");
+    if (g->dim != 3) return fail(TG_EINVAL, "tg_query_noalloc: 3-D grids only");
+    if (N < 0) return fail(TG_EINVAL, "tg_query_noalloc: N < 0");
+    if (N > kNoallocMaxPoints)
+        return fail(TG_EINVAL, "tg_query_noalloc: N = %lld exceeds the fixed scratch limit of %lld points",
+                    (long long)N, (long long)kNoallocMaxPoints);
+    if (N == 0) return TG_OK;
+    if (!pts || !out) return fail(TG_EINVAL, "tg_query_noalloc: NULL pts or out");
+    tg_batch b = {};
+    b.dim = 3;
+    b.res = g->res;
+    b.nbricks = 1;
+    for (int d = 0; d < 3; ++d) {
+        b.nb[d] = (g->res - 1 + kBrick - 1) / kBrick;
+        b.nbricks *= b.nb[d];
+    }
+    if (b.nbricks > kNoallocMaxBricks)
+        return fail(TG_EINVAL, "tg_query_noalloc: res = %d needs %lld bricks, over the fixed limit of %lld",
+                    g->res, (long long)b.nbricks, (long long)kNoallocMaxBricks);
+    NoallocScratch *s = nullptr;
+    tg_status st = scratch_address(&s);
+    if (st != TG_OK) return st;
+    b.max_points = kNoallocMaxPoints;
+    b.G = 0;                       // global-atomic binning: needs no per-chunk histogram
+    b.counts = s->counts;
+    b.offsets = s->offsets;
+    b.cursor = s->cursor;
+    b.hist = nullptr;
+    b.sorted = s->sorted;
+    b.status = s->status;
+    cudaGetDevice(&b.device);
+    st = cuda_status(cudaMemsetAsync(s->status, 0, sizeof(int), (cudaStream_t)stream), "tg_query_noalloc: clear status");
+    if (st != TG_OK) return st;
+    st = tg_batch_bin(&b, pts, N, stream);     // clears the brick counters before counting
+    if (st != TG_OK) return st;
+    return tg_query_binned(g, &b, out, grad_x, stream);
+}
