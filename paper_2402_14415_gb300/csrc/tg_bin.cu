@@ -17,6 +17,8 @@ constexpr int kBinThreads = 256;
 constexpr int kHistThreads = 1024;
 constexpr int kMaxSmemBins = 32768;   // 128 KB of shared counters
 constexpr int kColScanBricks = 32;    // bricks per block of the chunk-column scan
+constexpr int kCoarse = 64;           // bricks per coarse bin of the two-pass scatter
+constexpr int kFineThreads = 512;
 
 __device__ __forceinline__ void load_point3(const float *__restrict__ pts, int64_t n, float *x)
 {
@@ -147,13 +149,28 @@ bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int *
     if (threadIdx.x == 0) offsets[n] = carry;
 }
 
+// Coarse place: every chunk block writes its points, grouped by coarse bin
+// (kCoarse consecutive bricks), into the coarse array. A chunk's share of a
+// coarse bin is one contiguous run (hundreds of records), so the writes stream.
 __global__ void __launch_bounds__(kHistThreads)
-bin_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk, int res, int nbx, int nby, int nbricks,
-                 const int *__restrict__ hist, const int *__restrict__ offsets, float4 *__restrict__ sorted)
+bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk, int res, int nbx, int nby,
+                        int nbricks, const int *__restrict__ hist, const int *__restrict__ offsets,
+                        float4 *__restrict__ coarse)
 {
-    extern __shared__ int cur[];
+    __shared__ int cur[kMaxSmemBins / kCoarse];
+    const int ncoarse = (nbricks + kCoarse - 1) / kCoarse;
     const int *h = hist + (int64_t)blockIdx.x * nbricks;
-    for (int j = threadIdx.x; j < nbricks; j += blockDim.x) cur[j] = __ldg(offsets + j) + __ldg(h + j);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int cb = wid; cb < ncoarse; cb += blockDim.x >> 5) {     // one warp per coarse bin
+        int s = 0;
+        for (int j = lane; j < kCoarse; j += 32) {
+            const int b = cb * kCoarse + j;
+            if (b < nbricks) s += __ldg(h + b);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) cur[cb] = __ldg(offsets + cb * kCoarse) + s;
+    }
     __syncthreads();
     const float scale = (float)(res - 1);
     const int64_t lo = (int64_t)blockIdx.x * chunk;
@@ -174,13 +191,55 @@ bin_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk, int re
                 int c[3];
                 float t[3];
                 locate<3>(x[u], res, scale, c, t);
-                slot[u] = atomicAdd(cur + brick_of(c, nbx, nby), 1);
+                slot[u] = atomicAdd(cur + brick_of(c, nbx, nby) / kCoarse, 1);
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t n = n0 + (int64_t)u * blockDim.x;
-            if (n < hi) sorted[slot[u]] = make_float4(x[u][0], x[u][1], x[u][2], __int_as_float((int)n));
+            if (n < hi) coarse[slot[u]] = make_float4(x[u][0], x[u][1], x[u][2], __int_as_float((int)n));
+        }
+    }
+}
+
+// Fine place: one block per coarse bin scatters its records to their bricks.
+// The destination is the coarse bin's own region (about a megabyte), which
+// stays in L2 while the partial-sector writes merge.
+__global__ void __launch_bounds__(kFineThreads)
+bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int nby, int nbricks,
+                      const int *__restrict__ offsets, float4 *__restrict__ sorted)
+{
+    __shared__ int cur[kCoarse];
+    const int b0 = blockIdx.x * kCoarse;
+    const int nb = min(kCoarse, nbricks - b0);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) cur[j] = __ldg(offsets + b0 + j);
+    __syncthreads();
+    const int lo = __ldg(offsets + b0), hi = __ldg(offsets + b0 + nb);
+    const float scale = (float)(res - 1);
+    constexpr int U = 4;
+    for (int p0 = lo + threadIdx.x; p0 < hi; p0 += U * blockDim.x) {
+        float4 q[U];
+        int slot[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = p0 + u * blockDim.x;
+            if (p < hi) q[u] = coarse[p];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = p0 + u * blockDim.x;
+            if (p < hi) {
+                const float x[3] = {q[u].x, q[u].y, q[u].z};
+                int c[3];
+                float t[3];
+                locate<3>(x, res, scale, c, t);
+                slot[u] = atomicAdd(cur + brick_of(c, nbx, nby) - b0, 1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = p0 + u * blockDim.x;
+            if (p < hi) sorted[slot[u]] = q[u];
         }
     }
 }
@@ -301,13 +360,14 @@ tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
     if (st == TG_OK && b->G)
         st = cuda_status(cudaMalloc(&b->hist, (size_t)b->G * b->nbricks * sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->sorted, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
+    if (st == TG_OK && b->G)
+        st = cuda_status(cudaMalloc(&b->coarse, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->status, sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->offsets, 0, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->status, 0, sizeof(int)), "tg_batch_create");
     if (st == TG_OK && b->G) {
         const int bytes = (int)(b->nbricks * sizeof(int));
         st = set_smem((const void *)bin_hist_kernel, bytes);
-        if (st == TG_OK) st = set_smem((const void *)bin_place_kernel, bytes);
         if (st == TG_OK) st = set_smem((const void *)bin_chunk_scan_kernel, b->G * kColScanBricks * (int)sizeof(int));
     }
     if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_batch_create");
@@ -320,6 +380,7 @@ tg_status tg_batch_destroy(tg_batch *b)
 {
     if (!b) return TG_OK;
     cudaFree(b->counts); cudaFree(b->offsets); cudaFree(b->cursor); cudaFree(b->hist); cudaFree(b->sorted);
+    cudaFree(b->coarse);
     cudaFree(b->status);
     free(b);
     return TG_OK;
@@ -346,9 +407,12 @@ tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream strea
         if ((st = launch_status("tg_batch_bin: chunk scan")) != TG_OK) return st;
         bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, nullptr, nbr);
         if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;
-        bin_place_kernel<<<b->G, kHistThreads, smem, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist, b->offsets,
-                                                          b->sorted);
-        return launch_status("tg_batch_bin: place");
+        bin_coarse_place_kernel<<<b->G, kHistThreads, 0, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist,
+                                                              b->offsets, b->coarse);
+        if ((st = launch_status("tg_batch_bin: coarse place")) != TG_OK) return st;
+        bin_fine_place_kernel<<<(nbr + kCoarse - 1) / kCoarse, kFineThreads, 0, s>>>(b->coarse, b->res, nbx, nby, nbr,
+                                                                                     b->offsets, b->sorted);
+        return launch_status("tg_batch_bin: fine place");
     }
     if ((st = cuda_status(cudaMemsetAsync(b->counts, 0, (b->nbricks + 1) * sizeof(int), s), "tg_batch_bin")) != TG_OK)
         return st;

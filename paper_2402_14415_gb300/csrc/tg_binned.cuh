@@ -18,6 +18,7 @@ struct tg_batch {
     int *cursor;          // nbricks, scatter cursors (global-atomic binning)
     int *hist;            // G x nbricks chunk histograms, then chunk cursors
     float4 *sorted;       // max_points: (x, y, z, original index as int bits)
+    float4 *coarse;       // max_points: the same records grouped by coarse bin (histogram binning)
     int *status;          // device word: non-zero after a bounded wait gave up
     int device;
 };

@@ -1,0 +1,210 @@
+// Vertex-centric coefficient-gradient gather over one brick (the adjoint of
+// Eq. 2 - Eq. 4), shared by the binned backward and the fused training steps.
+//
+// The brick's staged points are sorted by cell in shared memory. Every
+// thread owns whole vertices: for a vertex it walks the points of its (up to)
+// eight incident cells - four contiguous ranges of the cell-sorted records,
+// one per incident cell row - and accumulates w_i phi_k(delta_i) s (+ the
+// spatial-gradient terms) in registers. No two threads ever write the same
+// vertex, so nothing is atomic. Vertices are counting-sorted by their load
+// (points in incident cells) before they are dealt to threads, so the lanes
+// of a warp carry nearly equal work.
+#pragma once
+
+#include "tg_binned.cuh"
+
+namespace tg {
+
+constexpr int kBrickVerts = kBV * kBV * kBV;   // 729
+constexpr int kMaxLoadBins = 64;               // vertex loads >= 63 share the last bin
+
+// Staged point record: t (3), s = dL/df (C) and, with a spatial-gradient
+// upstream, g = dL/d(grad_u f) in grid units (3 C); padded to 16 bytes.
+template <int C, bool HAS_G>
+struct GatherRec {
+    static constexpr int fields = 3 + C + (HAS_G ? 3 * C : 0);
+    static constexpr int stride = (fields + 3) / 4 * 4;
+};
+
+// Shared-memory integer workspace of the gather (counts, offsets, vertex order).
+struct GatherInts {
+    static constexpr int cell_cur = 0;                          // kBrickCells
+    static constexpr int cell_off = cell_cur + kBrickCells;     // kBrickCells + 1
+    static constexpr int vload_bins = cell_off + kBrickCells + 1 + 3;   // kMaxLoadBins
+    static constexpr int vorder = vload_bins + kMaxLoadBins;    // kBrickVerts
+    static constexpr int warp_tmp = vorder + kBrickVerts + 3;   // 32
+    static constexpr int total = warp_tmp + 32;
+};
+
+// Block-wide exclusive scan of one int per thread; returns the prefix and the total.
+template <int NT>
+__device__ __forceinline__ int gather_block_scan(int v, int *warp_tmp, int &total)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_tmp[wid] = incl;
+    __syncthreads();
+    int before = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int s = warp_tmp[w];
+        if (w < wid) before += s;
+        total += s;
+    }
+    __syncthreads();
+    return before + incl - v;
+}
+
+// Scan of the 512 cell counts in ints[cell_cur] into ints[cell_off] and back
+// into ints[cell_cur] (as placement cursors). All NT threads take part.
+template <int NT>
+__device__ __forceinline__ void gather_scan_cells(int *ints)
+{
+    static_assert(kBrickCells % NT == 0, "");
+    constexpr int CPT = kBrickCells / NT;
+    int *cur = ints + GatherInts::cell_cur, *off = ints + GatherInts::cell_off;
+    int v[CPT], sum = 0;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) { v[k] = cur[CPT * threadIdx.x + k]; sum += v[k]; }
+    int total;
+    int run = gather_block_scan<NT>(sum, ints + GatherInts::warp_tmp, total);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        off[CPT * threadIdx.x + k] = run;
+        cur[CPT * threadIdx.x + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) off[kBrickCells] = total;
+    __syncthreads();
+}
+
+// Load of vertex v: the points of its incident cells in this round.
+__device__ __forceinline__ int vertex_load(int v, const int *off)
+{
+    const int vx = v % kBV, vy = (v / kBV) % kBV, vz = v / (kBV * kBV);
+    const int xlo = max(vx - 1, 0), xhi = min(vx, kBrick - 1);
+    int n = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int cy = vy - (r & 1), cz = vz - (r >> 1);
+        if (cy >= 0 && cz >= 0 && cy < kBrick && cz < kBrick) {
+            const int row = kBrick * (cy + kBrick * cz);
+            n += off[row + xhi + 1] - off[row + xlo];
+        }
+    }
+    return n;
+}
+
+// Counting sort of the 729 vertices by load into ints[vorder] (heaviest first).
+template <int NT>
+__device__ __forceinline__ void gather_order_vertices(int *ints)
+{
+    int *bins = ints + GatherInts::vload_bins, *order = ints + GatherInts::vorder;
+    const int *off = ints + GatherInts::cell_off;
+    for (int j = threadIdx.x; j < kMaxLoadBins; j += NT) bins[j] = 0;
+    __syncthreads();
+    constexpr int VPT = (kBrickVerts + NT - 1) / NT;
+    int key[VPT];
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        const int v = threadIdx.x + k * NT;
+        key[k] = -1;
+        if (v < kBrickVerts) {
+            key[k] = kMaxLoadBins - 1 - min(vertex_load(v, off), kMaxLoadBins - 1);   // heavy first
+            atomicAdd(bins + key[k], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {   // exclusive scan of the 64 bins by one warp
+        int a = bins[2 * threadIdx.x], b = bins[2 * threadIdx.x + 1];
+        int incl = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)threadIdx.x >= o) incl += u;
+        }
+        const int ex = incl - a - b;
+        bins[2 * threadIdx.x] = ex;
+        bins[2 * threadIdx.x + 1] = ex + a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        if (key[k] >= 0) order[atomicAdd(bins + key[k], 1)] = threadIdx.x + k * NT;
+    }
+    __syncthreads();
+}
+
+// Accumulates into acc[NV] the contributions of all staged points of the
+// incident cells of vertex v (local coordinates).
+template <int ORDER, int C, bool HAS_G>
+__device__ __forceinline__ void gather_vertex(int v, const float *rec, const int *off, float *acc)
+{
+    constexpr int K = Basis<3, ORDER>::K;
+    constexpr int RS = GatherRec<C, HAS_G>::stride;
+    const int vx = v % kBV, vy = (v / kBV) % kBV, vz = v / (kBV * kBV);
+    const int xlo = max(vx - 1, 0), xhi = min(vx, kBrick - 1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int by = r & 1, bz = r >> 1;            // corner bits of v in the incident cells of this row
+        const int cy = vy - by, cz = vz - bz;
+        if (cy < 0 || cz < 0 || cy >= kBrick || cz >= kBrick) continue;
+        const int row = kBrick * (cy + kBrick * cz);
+        const int p_lo = off[row + xlo], p_hi = off[row + xhi + 1];
+        const int p_mid = off[row + vx];              // first point of cell vx (= p_hi when vx = 8)
+        for (int p = p_lo; p < p_hi; ++p) {
+            const float *q = rec + p * RS;
+            const float4 tq = *reinterpret_cast<const float4 *>(q);
+            const float t0 = tq.x, t1 = tq.y, t2 = tq.z;
+            const bool bx = p < p_mid;                // point in cell vx - 1: v is its +x corner
+            const float a0 = bx ? t0 : 1.f - t0;
+            const float a1 = by ? t1 : 1.f - t1;
+            const float a2 = bz ? t2 : 1.f - t2;
+            const float w = a0 * a1 * a2;
+            const float dl[3] = {bx ? t0 - 1.f : t0, by ? t1 - 1.f : t1, bz ? t2 - 1.f : t2};
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) {
+                float s = w * q[3 + ch];
+                float g[3];
+                if constexpr (HAS_G) {
+                    const float *gp = q + 3 + C + 3 * ch;
+                    const float dw0 = (bx ? 1.f : -1.f) * a1 * a2;
+                    const float dw1 = (by ? 1.f : -1.f) * a0 * a2;
+                    const float dw2 = (bz ? 1.f : -1.f) * a0 * a1;
+                    s = fmaf(dw0, gp[0], fmaf(dw1, gp[1], fmaf(dw2, gp[2], s)));
+                    g[0] = w * gp[0]; g[1] = w * gp[1]; g[2] = w * gp[2];
+                }
+                Basis<3, ORDER>::template accumulate<HAS_G>(s, g, dl, acc + ch * K);
+            }
+        }
+    }
+}
+
+// One gather round: all NT threads take the vertices in load order and add
+// their sums into the shared tile (row stride BXI floats, vertex stride NV).
+template <int ORDER, int C, bool HAS_G, int NT, int BXI>
+__device__ __forceinline__ void gather_round(const float *rec, int *ints, float *tile)
+{
+    constexpr int NV = Basis<3, ORDER>::K * C;
+    gather_order_vertices<NT>(ints);
+    const int *order = ints + GatherInts::vorder, *off = ints + GatherInts::cell_off;
+    for (int j = threadIdx.x; j < kBrickVerts; j += NT) {
+        const int v = order[j];
+        float acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.f;
+        gather_vertex<ORDER, C, HAS_G>(v, rec, off, acc);
+        float *d = tile + (v / kBV) * BXI + (v % kBV) * NV;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) d[k] += acc[k];
+    }
+}
+
+}  // namespace tg

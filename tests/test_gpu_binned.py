@@ -12,6 +12,7 @@ pytestmark = pytest.mark.gpu
 SHAPES = [  # res, order, C, dtype  (res - 1 not a multiple of 8: ragged last brick)
     (34, 2, 1, "f32"), (20, 1, 3, "f32"), (24, 0, 1, "f32"), (18, 2, 2, "f32"), (36, 2, 1, "bf16"),
     (28, 1, 1, "f16"), (10, 2, 1, "f32"),
+    (300, 0, 1, "f32"),      # more than 32768 bricks: the global-atomic binning path
 ]
 
 
