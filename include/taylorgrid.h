@@ -170,13 +170,32 @@ TG_API tg_status tg_batch_destroy(tg_batch *batch);
  * and the permutation; `pts` may be reused by the caller afterwards. */
 TG_API tg_status tg_batch_bin(tg_batch *batch, const float *pts, int64_t N, tg_stream stream);
 
-/* Same outputs as tg_query / tg_query_backward for the points last binned
- * (outputs and upstream gradients in the caller's original point order). */
+/* Order of the per-point arrays of the two calls below. */
+#define TG_ORDER_INPUT 0    /* the caller's original point order */
+#define TG_ORDER_BINNED 1   /* the batch's binned order (see tg_batch_order / tg_batch_points) */
+
+/* Same outputs as tg_query / tg_query_backward for the points last binned.
+ * With TG_ORDER_INPUT the per-point arrays (out, grad_x, dL_df, dL_dgradx)
+ * are in the caller's original order: the kernels work in binned order on a
+ * staging buffer and one extra pass scatters the outputs back (or gathers the
+ * upstream gradients). With TG_ORDER_BINNED they are in binned order and the
+ * extra pass is skipped - use it when the per-point work around the query
+ * (a loss, a sampler) can run in that order too. The staging buffer holds
+ * 4 floats per point from tg_batch_create; spatial gradients with more than
+ * one channel need more and the first such call grows it (synchronously).
+ * Errors: TG_EINVAL (shape or order flag), TG_ENOMEM, TG_EDEVICE. */
 TG_API tg_status tg_query_binned(const tg_grid *grid, const tg_batch *batch,
-                          float *out, float *grad_x, tg_stream stream);
+                                 float *out, float *grad_x, int order_flags, tg_stream stream);
 TG_API tg_status tg_query_backward_binned(const tg_grid *grid, const tg_batch *batch,
-                                   const float *dL_df, const float *dL_dgradx,
-                                   float *coef_grad, tg_stream stream);
+                                          const float *dL_df, const float *dL_dgradx,
+                                          float *coef_grad, int order_flags, tg_stream stream);
+
+/* The original index of every binned slot (device, N int32): slot p holds
+ * input point idx[p]. */
+TG_API tg_status tg_batch_order(const tg_batch *batch, int32_t *idx, tg_stream stream);
+
+/* The binned points in binned order (device, N x 3 FP32). */
+TG_API tg_status tg_batch_points(const tg_batch *batch, float *pts, tg_stream stream);
 
 /* The binned kernels wait on their TMA copies with a 2 s limit; a wait that
  * gives up sets a device flag instead of hanging. Synchronously reads that
@@ -191,11 +210,11 @@ TG_API tg_status tg_batch_timeouts(tg_batch *batch, int *timed_out);
  * them this call bins the N points (device, N x 3) and evaluates f (and, if
  * grad_x is not NULL, the world-unit spatial gradient) exactly like
  * tg_batch_bin + tg_query_binned, with all scratch held in one fixed array
- * of about 4.4 MB compiled into the library (every GPU that loads the
+ * of about 9.4 MB compiled into the library (every GPU that loads the
  * library keeps it until the process exits).
- * Limits: N <= 262144 points and res <= 257 (at most 32768 bricks); larger
- * requests fail with TG_EINVAL and a message. 3-D grids only, with the same
- * shape rules as tg_query_binned.
+ * Limits: N <= 262144 points and res <= 257 (at most 32768 bricks), and
+ * grad_x only for one-channel grids; other requests fail with TG_EINVAL and a
+ * message. 3-D grids only, with the same shape rules as tg_query_binned.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.
  * Every call reuses the same array and leaves its contents behind (the call

@@ -17,6 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtaylorgrid.so")
 
 TG_F32, TG_BF16, TG_F16 = 0, 1, 2
+TG_ORDER_INPUT, TG_ORDER_BINNED = 0, 1
 DTYPES = {"f32": TG_F32, "fp32": TG_F32, "float32": TG_F32, "bf16": TG_BF16, "bfloat16": TG_BF16,
           "f16": TG_F16, "fp16": TG_F16, "float16": TG_F16}
 STATUS = {0: "TG_OK", 1: "TG_EINVAL", 2: "TG_ENOMEM", 3: "TG_EBUDGET", 4: "TG_ETIMEOUT", 5: "TG_EDEVICE",
@@ -59,8 +60,10 @@ _SIGS = {
     "tg_batch_create": [_int, _int, _i64, ctypes.POINTER(_vp)],
     "tg_batch_destroy": [_vp],
     "tg_batch_bin": [_vp, _vp, _i64, _vp],
-    "tg_query_binned": [_vp, _vp, _vp, _vp, _vp],
-    "tg_query_backward_binned": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "tg_query_binned": [_vp, _vp, _vp, _vp, _int, _vp],
+    "tg_query_backward_binned": [_vp, _vp, _vp, _vp, _vp, _int, _vp],
+    "tg_batch_order": [_vp, _vp, _vp],
+    "tg_batch_points": [_vp, _vp, _vp],
     "tg_batch_timeouts": [_vp, ctypes.POINTER(_int)],
     "tg_query_noalloc": [_vp, _vp, _i64, _vp, _vp, _vp],
     "tg_adam_step": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
@@ -231,7 +234,8 @@ def tg_batch_bin(batch: Batch, pts: torch.Tensor, stream=None):
     return batch
 
 
-def tg_query_binned(grid: Grid, batch: Batch, out=None, grad_x=None, want_grad=False, stream=None):
+def tg_query_binned(grid: Grid, batch: Batch, out=None, grad_x=None, want_grad=False, binned_order=False,
+                    stream=None):
     N = batch.n
     dev = torch.device("cuda")
     if out is None:
@@ -240,18 +244,37 @@ def tg_query_binned(grid: Grid, batch: Batch, out=None, grad_x=None, want_grad=F
         grad_x = torch.empty((N, grid.channels, grid.dim), device=dev, dtype=torch.float32)
     _check(load().tg_query_binned(grid.handle, batch.handle, _ptr(out, "out", numel=N * grid.channels),
                                   _ptr(grad_x, "grad_x", numel=N * grid.channels * grid.dim, optional=True),
-                                  _stream(stream)), "tg_query_binned")
+                                  TG_ORDER_BINNED if binned_order else TG_ORDER_INPUT, _stream(stream)),
+           "tg_query_binned")
     return (out, grad_x) if (want_grad or grad_x is not None) else out
 
 
-def tg_query_backward_binned(grid: Grid, batch: Batch, dL_df, coef_grad, dL_dgradx=None, stream=None):
+def tg_query_backward_binned(grid: Grid, batch: Batch, dL_df, coef_grad, dL_dgradx=None, binned_order=False,
+                             stream=None):
     N = batch.n
     _check(load().tg_query_backward_binned(grid.handle, batch.handle, _ptr(dL_df, "dL_df", numel=N * grid.channels),
                                            _ptr(dL_dgradx, "dL_dgradx", numel=N * grid.channels * grid.dim,
                                                 optional=True),
-                                           _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), _stream(stream)),
+                                           _ptr(coef_grad, "coef_grad", numel=grid.n_coefs),
+                                           TG_ORDER_BINNED if binned_order else TG_ORDER_INPUT, _stream(stream)),
            "tg_query_backward_binned")
     return coef_grad
+
+
+def tg_batch_order(batch: Batch, stream=None) -> torch.Tensor:
+    """Original index of every binned slot (int32, N)."""
+    idx = torch.empty(batch.n, device="cuda", dtype=torch.int32)
+    _check(load().tg_batch_order(batch.handle, _ptr(idx, "idx", torch.int32) if batch.n else None, _stream(stream)),
+           "tg_batch_order")
+    return idx
+
+
+def tg_batch_points(batch: Batch, stream=None) -> torch.Tensor:
+    """The binned points in binned order (N, 3)."""
+    pts = torch.empty((batch.n, 3), device="cuda", dtype=torch.float32)
+    _check(load().tg_batch_points(batch.handle, _ptr(pts, "pts") if batch.n else None, _stream(stream)),
+           "tg_batch_points")
+    return pts
 
 
 def tg_batch_timeouts(batch: Batch) -> int:

@@ -2,9 +2,12 @@
 //
 // With at most 32768 bricks each of G chunk blocks builds a shared-memory
 // histogram of its slice of the points, a column scan over the chunks turns
-// the histograms into per-chunk write cursors, and the place pass writes every
-// point once into brick order using shared-memory atomics only. Larger grids
-// fall back to global-atomic counting.
+// the histograms into per-chunk write cursors, and two place passes (coarse
+// runs, then a fine scatter inside an L2-resident region) write every point
+// into brick order using shared-memory atomics only. Larger grids fall back
+// to global-atomic counting. The binning also records the permutation, so
+// the brick kernels read and write in binned order and the original order is
+// restored (or gathered) by one separate pass over an L2-sized array.
 #include <stdlib.h>
 
 #include <mutex>
@@ -207,7 +210,7 @@ bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk,
 // stays in L2 while the partial-sector writes merge.
 __global__ void __launch_bounds__(kFineThreads)
 bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int nby, int nbricks,
-                      const int *__restrict__ offsets, float4 *__restrict__ sorted)
+                      const int *__restrict__ offsets, float4 *__restrict__ sorted, int *__restrict__ perm)
 {
     __shared__ int cur[kCoarse];
     const int b0 = blockIdx.x * kCoarse;
@@ -239,7 +242,10 @@ bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int n
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int p = p0 + u * blockDim.x;
-            if (p < hi) sorted[slot[u]] = q[u];
+            if (p < hi) {
+                sorted[slot[u]] = q[u];
+                perm[slot[u]] = __float_as_int(q[u].w);
+            }
         }
     }
 }
@@ -259,7 +265,7 @@ bin_count_kernel(const float *__restrict__ pts, int64_t N, int res, int nbx, int
 
 __global__ void __launch_bounds__(kBinThreads)
 bin_scatter_kernel(const float *__restrict__ pts, int64_t N, int res, int nbx, int nby, int *__restrict__ cursor,
-                   float4 *__restrict__ sorted)
+                   float4 *__restrict__ sorted, int *__restrict__ perm)
 {
     const float scale = (float)(res - 1);
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
@@ -269,6 +275,48 @@ bin_scatter_kernel(const float *__restrict__ pts, int64_t N, int res, int nbx, i
         locate<3>(x, res, scale, c, t);
         const int slot = atomicAdd(cursor + brick_of(c, nbx, nby), 1);
         sorted[slot] = make_float4(x[0], x[1], x[2], __int_as_float((int)n));
+        perm[slot] = (int)n;
+    }
+}
+
+// Original-order outputs from binned-order staging: out[perm[p]] = stage[p].
+__global__ void __launch_bounds__(256)
+unpermute_kernel(const int *__restrict__ perm, const float *__restrict__ stage, int64_t N, int C,
+                 float *__restrict__ out, float *__restrict__ gx)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = __ldg(perm + p);
+        for (int ch = 0; ch < C; ++ch) out[n * C + ch] = __ldg(stage + p * C + ch);
+        if (gx) {
+            const float *g = stage + N * C + p * 3 * C;
+            for (int j = 0; j < 3 * C; ++j) gx[n * 3 * C + j] = __ldg(g + j);
+        }
+    }
+}
+
+// Binned-order upstream gradients: stage[p] = dLdf[perm[p]] (then dLdg).
+__global__ void __launch_bounds__(256)
+gather_upstream_kernel(const int *__restrict__ perm, const float *__restrict__ dLdf, const float *__restrict__ dLdg,
+                       int64_t N, int C, float *__restrict__ stage)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = __ldg(perm + p);
+        for (int ch = 0; ch < C; ++ch) stage[p * C + ch] = __ldg(dLdf + n * C + ch);
+        if (dLdg) {
+            float *g = stage + N * C + p * 3 * C;
+            for (int j = 0; j < 3 * C; ++j) g[j] = __ldg(dLdg + n * 3 * C + j);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+batch_points_kernel(const float4 *__restrict__ sorted, int64_t N, float *__restrict__ pts)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const float4 q = sorted[p];
+        pts[3 * p] = q.x;
+        pts[3 * p + 1] = q.y;
+        pts[3 * p + 2] = q.z;
     }
 }
 
@@ -331,6 +379,39 @@ static unsigned grid_for(const void *kernel, int threads, int64_t N)
     return (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
 }
 
+tg_status ensure_stage(tg_batch *bt, int64_t floats, const char *who)
+{
+    if (bt->stage_floats >= floats) return TG_OK;
+    if (!bt->stage_owned && bt->stage)
+        return fail(TG_EINVAL, "%s: the request needs %lld staging floats, the fixed scratch holds %lld", who,
+                    (long long)floats, (long long)bt->stage_floats);
+    float *p = nullptr;
+    tg_status st = cuda_status(cudaMalloc(&p, (size_t)floats * sizeof(float)), who);
+    if (st != TG_OK) return st;
+    if (bt->stage) {
+        cudaDeviceSynchronize();
+        cudaFree(bt->stage);
+    }
+    bt->stage = p;
+    bt->stage_floats = floats;
+    bt->stage_owned = true;
+    return TG_OK;
+}
+
+tg_status unpermute_outputs(const tg_batch *bt, int C, float *out, float *grad_x, cudaStream_t s)
+{
+    unpermute_kernel<<<grid_for((const void *)unpermute_kernel, 256, bt->n), 256, 0, s>>>(bt->perm, bt->stage, bt->n,
+                                                                                          C, out, grad_x);
+    return launch_status("tg_query_binned: unpermute");
+}
+
+tg_status gather_upstream(const tg_batch *bt, int C, const float *dL_df, const float *dL_dgradx, cudaStream_t s)
+{
+    gather_upstream_kernel<<<grid_for((const void *)gather_upstream_kernel, 256, bt->n), 256, 0, s>>>(
+        bt->perm, dL_df, dL_dgradx, bt->n, C, bt->stage);
+    return launch_status("tg_query_backward_binned: gather upstream");
+}
+
 }  // namespace tg
 
 using namespace tg;
@@ -362,6 +443,12 @@ tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->sorted, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
     if (st == TG_OK && b->G)
         st = cuda_status(cudaMalloc(&b->coarse, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->perm, (max_points > 0 ? max_points : 1) * sizeof(int)), "tg_batch_create");
+    if (st == TG_OK) {
+        b->stage_floats = 4 * (max_points > 0 ? max_points : 1);
+        b->stage_owned = true;
+        st = cuda_status(cudaMalloc(&b->stage, (size_t)b->stage_floats * sizeof(float)), "tg_batch_create");
+    }
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->status, sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->offsets, 0, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->status, 0, sizeof(int)), "tg_batch_create");
@@ -381,6 +468,8 @@ tg_status tg_batch_destroy(tg_batch *b)
     if (!b) return TG_OK;
     cudaFree(b->counts); cudaFree(b->offsets); cudaFree(b->cursor); cudaFree(b->hist); cudaFree(b->sorted);
     cudaFree(b->coarse);
+    cudaFree(b->perm);
+    if (b->stage_owned) cudaFree(b->stage);
     cudaFree(b->status);
     free(b);
     return TG_OK;
@@ -411,7 +500,7 @@ tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream strea
                                                               b->offsets, b->coarse);
         if ((st = launch_status("tg_batch_bin: coarse place")) != TG_OK) return st;
         bin_fine_place_kernel<<<(nbr + kCoarse - 1) / kCoarse, kFineThreads, 0, s>>>(b->coarse, b->res, nbx, nby, nbr,
-                                                                                     b->offsets, b->sorted);
+                                                                                     b->offsets, b->sorted, b->perm);
         return launch_status("tg_batch_bin: fine place");
     }
     if ((st = cuda_status(cudaMemsetAsync(b->counts, 0, (b->nbricks + 1) * sizeof(int), s), "tg_batch_bin")) != TG_OK)
@@ -422,8 +511,27 @@ tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream strea
     bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, b->cursor, nbr);
     if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;
     bin_scatter_kernel<<<grid_for((const void *)bin_scatter_kernel, kBinThreads, N), kBinThreads, 0, s>>>(
-        pts, N, b->res, nbx, nby, b->cursor, b->sorted);
+        pts, N, b->res, nbx, nby, b->cursor, b->sorted, b->perm);
     return launch_status("tg_batch_bin: scatter");
+}
+
+tg_status tg_batch_order(const tg_batch *b, int32_t *idx, tg_stream stream)
+{
+    if (!b) return fail(TG_EINVAL, "tg_batch_order: batch is NULL");
+    if (b->n == 0) return TG_OK;
+    if (!idx) return fail(TG_EINVAL, "tg_batch_order: idx is NULL");
+    return cuda_status(cudaMemcpyAsync(idx, b->perm, (size_t)b->n * sizeof(int), cudaMemcpyDeviceToDevice,
+                                       (cudaStream_t)stream), "tg_batch_order");
+}
+
+tg_status tg_batch_points(const tg_batch *b, float *pts, tg_stream stream)
+{
+    if (!b) return fail(TG_EINVAL, "tg_batch_points: batch is NULL");
+    if (b->n == 0) return TG_OK;
+    if (!pts) return fail(TG_EINVAL, "tg_batch_points: pts is NULL");
+    batch_points_kernel<<<grid_for((const void *)batch_points_kernel, 256, b->n), 256, 0, (cudaStream_t)stream>>>(
+        b->sorted, b->n, pts);
+    return launch_status("tg_batch_points");
 }
 
 tg_status tg_batch_timeouts(tg_batch *b, int *timed_out)

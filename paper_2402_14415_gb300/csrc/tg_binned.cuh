@@ -19,6 +19,10 @@ struct tg_batch {
     int *hist;            // G x nbricks chunk histograms, then chunk cursors
     float4 *sorted;       // max_points: (x, y, z, original index as int bits)
     float4 *coarse;       // max_points: the same records grouped by coarse bin (histogram binning)
+    int *perm;            // max_points: original index of every binned slot
+    float *stage;         // binned-order staging of outputs / upstream gradients
+    int64_t stage_floats; // capacity of stage
+    bool stage_owned;     // stage was allocated by the batch (false: caller-provided scratch)
     int *status;          // device word: non-zero after a bounded wait gave up
     int device;
 };
@@ -53,5 +57,14 @@ tg_status make_brick_map(CUtensorMap *map, const void *base, CUtensorMapDataType
 tg_status set_smem(const void *kernel, int bytes);
 
 tg_status check_pair(const tg_grid *g, const tg_batch *bt, const char *who);
+
+// Makes bt->stage hold at least `floats` floats (grows a batch-owned buffer
+// synchronously; a caller-provided buffer that is too small is an error).
+tg_status ensure_stage(tg_batch *bt, int64_t floats, const char *who);
+
+// out[perm[p]] = stage[p] (and the spatial-gradient block that follows it).
+tg_status unpermute_outputs(const tg_batch *bt, int C, float *out, float *grad_x, cudaStream_t s);
+// stage[p] = dL_df[perm[p]] (and dL_dgradx after it).
+tg_status gather_upstream(const tg_batch *bt, int C, const float *dL_df, const float *dL_dgradx, cudaStream_t s);
 
 }  // namespace tg

@@ -57,7 +57,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
         __syncthreads();
         int my_lc[kPPT];
         float my_t[kPPT][3];
-        int my_n[kPPT];
+        int my_n[kPPT];                              // binned slot of the point (upstream index)
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int i = tid + r * kBwdThreads;
@@ -67,7 +67,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
                 const float x[3] = {q.x, q.y, q.z};
                 int c[3];
                 locate<3>(x, res, scale, c, my_t[r]);
-                my_n[r] = __float_as_int(q.w);
+                my_n[r] = base + i;
                 my_lc[r] = (c[0] - x0) + kBrick * ((c[1] - y0) + kBrick * (c[2] - z0));
                 atomicAdd(cell_cur + my_lc[r], 1);
             }
@@ -139,15 +139,26 @@ static tg_status binned_bwd(const tg_grid *g, const tg_batch *bt, const float *u
 
 using namespace tg;
 
-extern "C" tg_status tg_query_backward_binned(const tg_grid *g, const tg_batch *bt, const float *dL_df,
-                                              const float *dL_dgradx, float *coef_grad, tg_stream stream)
+extern "C" tg_status tg_query_backward_binned(const tg_grid *g, const tg_batch *bt_in, const float *dL_df,
+                                              const float *dL_dgradx, float *coef_grad, int flags, tg_stream stream)
 {
-    tg_status st = check_pair(g, bt, "tg_query_backward_binned");
+    tg_status st = check_pair(g, bt_in, "tg_query_backward_binned");
     if (st != TG_OK) return st;
+    if (flags != TG_ORDER_INPUT && flags != TG_ORDER_BINNED)
+        return fail(TG_EINVAL, "tg_query_backward_binned: bad flags");
+    tg_batch *bt = const_cast<tg_batch *>(bt_in);
     if (bt->n == 0) return TG_OK;
     if (!dL_df || !coef_grad) return fail(TG_EINVAL, "tg_query_backward_binned: NULL dL_df or coef_grad");
     cudaStream_t s = (cudaStream_t)stream;
-#define TG_BB(D, O, C) binned_bwd<D, O, C>(g, bt, dL_df, dL_dgradx, coef_grad, s)
+    const float *uf = dL_df, *ug = dL_dgradx;
+    if (flags == TG_ORDER_INPUT) {
+        const int64_t need = bt->n * g->C * (dL_dgradx ? 4 : 1);
+        if ((st = ensure_stage(bt, need, "tg_query_backward_binned")) != TG_OK) return st;
+        if ((st = gather_upstream(bt, g->C, dL_df, dL_dgradx, s)) != TG_OK) return st;
+        uf = bt->stage;
+        ug = dL_dgradx ? bt->stage + bt->n * g->C : nullptr;
+    }
+#define TG_BB(D, O, C) binned_bwd<D, O, C>(g, bt, uf, ug, coef_grad, s)
     return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_BB);
 #undef TG_BB
 }

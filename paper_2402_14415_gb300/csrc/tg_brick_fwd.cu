@@ -1,7 +1,8 @@
 // Brick-binned forward query (Eq. 2 - Eq. 4): one block per 8^3-cell brick
 // TMA-loads the brick's 9^3 vertex blocks into shared memory with one 3-D
 // tiled copy, then evaluates its points from there using per-point delta
-// tables (one FMA per coefficient and corner).
+// tables (one FMA per coefficient and corner). Outputs are written in binned
+// order (coalesced); original order is restored by one separate pass.
 #include "tg_binned.cuh"
 
 namespace tg {
@@ -77,7 +78,7 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
     const float scale = (float)(res - 1);
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const float4 q = sorted[p];
-        const int64_t n = __float_as_int(q.w);
+        const int64_t n = p;                       // binned-order output slot
         const float x[3] = {q.x, q.y, q.z};
         int c[3];
         float t[3];
@@ -157,17 +158,29 @@ struct BinnedFwd {
 
 using namespace tg;
 
-extern "C" tg_status tg_query_binned(const tg_grid *g, const tg_batch *bt, float *out, float *grad_x, tg_stream stream)
+extern "C" tg_status tg_query_binned(const tg_grid *g, const tg_batch *bt_in, float *out, float *grad_x, int flags,
+                                     tg_stream stream)
 {
-    tg_status st = check_pair(g, bt, "tg_query_binned");
+    tg_status st = check_pair(g, bt_in, "tg_query_binned");
     if (st != TG_OK) return st;
+    if (flags != TG_ORDER_INPUT && flags != TG_ORDER_BINNED) return fail(TG_EINVAL, "tg_query_binned: bad flags");
+    tg_batch *bt = const_cast<tg_batch *>(bt_in);
     if (bt->n == 0) return TG_OK;
     if (!out) return fail(TG_EINVAL, "tg_query_binned: out is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-#define TG_QB(D, O, C)                                                                      \
-    (g->dtype == TG_F32    ? BinnedFwd<float>::run<D, O, C>(g, bt, out, grad_x, s)          \
-     : g->dtype == TG_BF16 ? BinnedFwd<__nv_bfloat16>::run<D, O, C>(g, bt, out, grad_x, s)  \
-                           : BinnedFwd<__half>::run<D, O, C>(g, bt, out, grad_x, s))
-    return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_QB);
+    float *o = out, *gx = grad_x;
+    if (flags == TG_ORDER_INPUT) {
+        const int64_t need = bt->n * g->C * (grad_x ? 4 : 1);
+        if ((st = ensure_stage(bt, need, "tg_query_binned")) != TG_OK) return st;
+        o = bt->stage;
+        gx = grad_x ? bt->stage + bt->n * g->C : nullptr;
+    }
+#define TG_QB(D, O, C)                                                                  \
+    (g->dtype == TG_F32    ? BinnedFwd<float>::run<D, O, C>(g, bt, o, gx, s)            \
+     : g->dtype == TG_BF16 ? BinnedFwd<__nv_bfloat16>::run<D, O, C>(g, bt, o, gx, s)    \
+                           : BinnedFwd<__half>::run<D, O, C>(g, bt, o, gx, s))
+    st = TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_QB);
 #undef TG_QB
+    if (st != TG_OK || flags == TG_ORDER_BINNED) return st;
+    return unpermute_outputs(bt, g->C, out, grad_x, s);
 }

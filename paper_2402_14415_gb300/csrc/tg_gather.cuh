@@ -151,38 +151,50 @@ __device__ __forceinline__ void gather_vertex(int v, const float *rec, const int
     constexpr int RS = GatherRec<C, HAS_G>::stride;
     const int vx = v % kBV, vy = (v / kBV) % kBV, vz = v / (kBV * kBV);
     const int xlo = max(vx - 1, 0), xhi = min(vx, kBrick - 1);
+    // The four incident cell rows r = (by, bz): point ranges [lo_r, lo_r + len_r)
+    // and the first point of cell vx in each (points before it have bx = 1).
+    int lo[4], len[4], mid[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const int by = r & 1, bz = r >> 1;            // corner bits of v in the incident cells of this row
-        const int cy = vy - by, cz = vz - bz;
-        if (cy < 0 || cz < 0 || cy >= kBrick || cz >= kBrick) continue;
-        const int row = kBrick * (cy + kBrick * cz);
-        const int p_lo = off[row + xlo], p_hi = off[row + xhi + 1];
-        const int p_mid = off[row + vx];              // first point of cell vx (= p_hi when vx = 8)
-        for (int p = p_lo; p < p_hi; ++p) {
-            const float *q = rec + p * RS;
-            const float4 tq = *reinterpret_cast<const float4 *>(q);
-            const float t0 = tq.x, t1 = tq.y, t2 = tq.z;
-            const bool bx = p < p_mid;                // point in cell vx - 1: v is its +x corner
-            const float a0 = bx ? t0 : 1.f - t0;
-            const float a1 = by ? t1 : 1.f - t1;
-            const float a2 = bz ? t2 : 1.f - t2;
-            const float w = a0 * a1 * a2;
-            const float dl[3] = {bx ? t0 - 1.f : t0, by ? t1 - 1.f : t1, bz ? t2 - 1.f : t2};
+        const int cy = vy - (r & 1), cz = vz - (r >> 1);
+        lo[r] = len[r] = mid[r] = 0;
+        if (cy >= 0 && cz >= 0 && cy < kBrick && cz < kBrick) {
+            const int row = kBrick * (cy + kBrick * cz);
+            lo[r] = off[row + xlo];
+            len[r] = off[row + xhi + 1] - lo[r];
+            mid[r] = off[row + vx];                   // = end of the row when vx = 8
+        }
+    }
+    const int e0 = len[0], e1 = e0 + len[1], e2 = e1 + len[2], total = e2 + len[3];
+    // One flat loop over the four ranges keeps a lane's trip count equal to
+    // its (load-balanced) total.
+    for (int j = 0; j < total; ++j) {
+        const int r = (j < e0) ? 0 : (j < e1) ? 1 : (j < e2) ? 2 : 3;
+        const int start = r == 0 ? 0 : r == 1 ? e0 : r == 2 ? e1 : e2;
+        const int p = (r == 0 ? lo[0] : r == 1 ? lo[1] : r == 2 ? lo[2] : lo[3]) + (j - start);
+        const int pm = r == 0 ? mid[0] : r == 1 ? mid[1] : r == 2 ? mid[2] : mid[3];
+        const bool bx = p < pm, by = r & 1, bz = r >> 1;
+        const float *q = rec + p * RS;
+        const float4 tq = *reinterpret_cast<const float4 *>(q);
+        const float t0 = tq.x, t1 = tq.y, t2 = tq.z;
+        const float a0 = bx ? t0 : 1.f - t0;
+        const float a1 = by ? t1 : 1.f - t1;
+        const float a2 = bz ? t2 : 1.f - t2;
+        const float w = a0 * a1 * a2;
+        const float dl[3] = {bx ? t0 - 1.f : t0, by ? t1 - 1.f : t1, bz ? t2 - 1.f : t2};
 #pragma unroll
-            for (int ch = 0; ch < C; ++ch) {
-                float s = w * q[3 + ch];
-                float g[3];
-                if constexpr (HAS_G) {
-                    const float *gp = q + 3 + C + 3 * ch;
-                    const float dw0 = (bx ? 1.f : -1.f) * a1 * a2;
-                    const float dw1 = (by ? 1.f : -1.f) * a0 * a2;
-                    const float dw2 = (bz ? 1.f : -1.f) * a0 * a1;
-                    s = fmaf(dw0, gp[0], fmaf(dw1, gp[1], fmaf(dw2, gp[2], s)));
-                    g[0] = w * gp[0]; g[1] = w * gp[1]; g[2] = w * gp[2];
-                }
-                Basis<3, ORDER>::template accumulate<HAS_G>(s, g, dl, acc + ch * K);
+        for (int ch = 0; ch < C; ++ch) {
+            float s = w * (ch == 0 ? tq.w : q[3 + ch]);
+            float g[3];
+            if constexpr (HAS_G) {
+                const float *gp = q + 3 + C + 3 * ch;
+                const float dw0 = (bx ? 1.f : -1.f) * a1 * a2;
+                const float dw1 = (by ? 1.f : -1.f) * a0 * a2;
+                const float dw2 = (bz ? 1.f : -1.f) * a0 * a1;
+                s = fmaf(dw0, gp[0], fmaf(dw1, gp[1], fmaf(dw2, gp[2], s)));
+                g[0] = w * gp[0]; g[1] = w * gp[1]; g[2] = w * gp[2];
             }
+            Basis<3, ORDER>::template accumulate<HAS_G>(s, g, dl, acc + ch * K);
         }
     }
 }

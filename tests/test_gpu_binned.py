@@ -49,6 +49,36 @@ def test_binned_forward_backward_parity(tg, res, order, C, dtype):
     check_coef_grad(grad.cpu().numpy(), 3, res, order, C, pts, dLdf, dLdg)
 
 
+@pytest.mark.parametrize("C,order", [(1, 2), (3, 1)])
+def test_binned_order_io(tg, C, order):
+    """TG_ORDER_BINNED outputs/upstreams equal the input-order ones through the batch permutation."""
+    res = 26
+    coefs = W.init_coefs(3, res, order, C, seed=2, std=0.4)
+    g = tg.tg_create(3, res, order, C, "f32")
+    tg.tg_set_coefs(g, to_dev(coefs))
+    pts = np.concatenate([points(3, res, 30000, seed=9), clustered(1000)])
+    N = pts.shape[0]
+    batch = tg.tg_batch_create(3, res, N)
+    tg.tg_batch_bin(batch, to_dev(pts))
+    idx = tg.tg_batch_order(batch).long()
+    assert torch.equal(torch.sort(idx).values, torch.arange(N, device="cuda"))
+    torch.testing.assert_close(tg.tg_batch_points(batch), to_dev(pts)[idx], rtol=0, atol=0, equal_nan=True)
+    out_i, gx_i = tg.tg_query_binned(g, batch, want_grad=True)
+    out_b, gx_b = tg.tg_query_binned(g, batch, want_grad=True, binned_order=True)
+    assert torch.equal(out_b, out_i[idx]) and torch.equal(gx_b, gx_i[idx])
+    r = np.random.default_rng(5)
+    uf = to_dev(r.normal(size=(N, C)).astype(np.float32))
+    ug = to_dev(r.normal(size=(N, C, 3)).astype(np.float32))
+    g_i = torch.zeros(g.n_coefs, device="cuda")
+    g_b = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward_binned(g, batch, uf, g_i, dL_dgradx=ug)
+    tg.tg_query_backward_binned(g, batch, uf[idx].contiguous(), g_b, dL_dgradx=ug[idx].contiguous(), binned_order=True)
+    torch.cuda.synchronize()
+    check_coef_grad(g_b.cpu().numpy(), 3, res, order, C, pts, uf.cpu().numpy(), ug.cpu().numpy())
+    # bricks sharing a face add into the gradient in either order (L2 reduce-add): FP32 rounding only
+    torch.testing.assert_close(g_b, g_i, rtol=1e-4, atol=1e-4)
+
+
 def test_binned_value_only_backward_and_rebin(tg):
     res, order, C = 26, 2, 1
     g = tg.tg_create(3, res, order, C, "f32", seed=3, init_std=0.3)
