@@ -18,8 +18,8 @@
  *    diagonal only and each off-diagonal entry appears once):
  *        3-D: f, g_x, g_y, g_z, H_xx, H_yy, H_zz, H_xy, H_xz, H_yz
  *        2-D: f, g_x, g_y, H_xx, H_yy, H_xy
- *    Derivatives are taken with respect to grid units u = x (res - 1): the
- *    offset of Eq. 3 is delta = t - b_i in [-1, 1]^D.
+ *    Derivatives are taken with respect to the world coordinates x, as in
+ *    Eq. 1: the offset of Eq. 3 is delta = x - v_i = (t - b_i) / (res - 1).
  *  - Exchange layout (tg_set_coefs / tg_get_coefs / coefficient gradients):
  *    FP32 [vertex][channel][k], vertex = x + res (y + res z). The library's
  *    device layout of the stored coefficients is the same order, in the
@@ -241,6 +241,54 @@ typedef struct {
  * moments (synchronously), so make it before any stream capture.
  * Errors: TG_EINVAL (NULL, step < 1), TG_ENOMEM, TG_EDEVICE. */
 TG_API tg_status tg_adam_step(tg_grid *grid, float *coef_grad, const tg_adam *params, tg_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * SDF fitting (Sec. 3.2). The target S is the zero level set of an analytic
+ * signed distance (Eq. 5): a union of spheres and axis-aligned boxes.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int n_spheres;
+    int n_boxes;
+    const float *spheres;    /* (device) n_spheres x (cx, cy, cz, r) */
+    const float *boxes;      /* (device) n_boxes x (cx, cy, cz, hx, hy, hz) */
+    const float *area_cdf;   /* (device) n_spheres + n_boxes cumulative surface-area fractions, last = 1
+                                (spheres first); used by the sampler only */
+} tg_shape;
+
+/* Signed distance of the union at N points (device, N x 3, clamped to
+ * [0,1]^3 like a query) into d (device, N). */
+TG_API tg_status tg_sdf_eval_target(const tg_shape *shape, const float *pts, int64_t N, float *d,
+                                    tg_stream stream);
+
+/* Fit batch of step `step`: the first N/2 points uniform in [0,1]^3, the rest
+ * near the surface (an area-weighted surface point of a member, kept if it is
+ * not inside another member, up to 8 attempts, else a uniform point; plus
+ * N(0, jitter^2) noise per axis, clamped). Every draw is the counter-based
+ * generator (seed, stream step*256 + a, index 16 j + slot); the same
+ * definition is implemented by the input generator of the tests. */
+TG_API tg_status tg_sample_sdf_points(const tg_shape *shape, uint64_t seed, int64_t step, int64_t N,
+                                      float jitter, float *pts, tg_stream stream);
+
+/* One SDF fitting step on a 3-D one-channel grid (Sec. 3.2):
+ *   L = mean_P |f(x) - d(x)|  +  lambda_eik * mean_P (||grad_x f(x)|| - 1)^2
+ * (Eq. 6 with w = 1, IGR's eikonal term of Eq. 8). The points are `pts`
+ * (device, N x 3) or, if pts is NULL, the fit batch of (seed, step) drawn on
+ * the device. The points are binned into `batch` (created for the grid's
+ * res, max_points >= N), the forward, the per-point loss and the backward run
+ * in binned order, and dL/dtheta is ADDED to coef_grad (device, n_coefs).
+ * loss_sums (device, 2 floats, accumulated) receives sum |f - d| and
+ * sum (||grad_x f|| - 1)^2 over the batch. sign(0) = 0; points whose spatial
+ * gradient has norm below 1e-12 get no eikonal gradient.
+ * The first call may grow the batch's staging buffer (11 floats per point). */
+TG_API tg_status tg_sdf_step(const tg_grid *grid, tg_batch *batch, const tg_shape *shape, const float *pts,
+                             int64_t N, uint64_t seed, int64_t step, float lambda_eik, float *coef_grad,
+                             float *loss_sums, tg_stream stream);
+
+/* Accumulates sum_P |f(x) - d(x)| over N points (device, N x 3) into
+ * err_sum (device, 1 float): the mean |SDF error| of a fit is err_sum / N.
+ * 3-D one-channel grids. */
+TG_API tg_status tg_sdf_error(const tg_grid *grid, const tg_shape *shape, const float *pts, int64_t N,
+                              float *err_sum, tg_stream stream);
 
 #ifdef __cplusplus
 }

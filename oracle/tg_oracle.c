@@ -9,7 +9,9 @@
  *
  * Conventions (readings of points the paper leaves open):
  *  - Domain [0,1]^D, `res` vertices per axis, vertex j at x = j/(res-1).
- *  - Offsets x - v_i (Eq. 3) are measured in grid units, delta = t - b_i in [-1,1]^D.
+ *  - Offsets x - v_i (Eq. 3) are world coordinates, delta = (t - b_i) h with
+ *    h = 1 / (res - 1): the stored series are the derivatives of f with
+ *    respect to x, as Eq. 1 writes them.
  *  - Corner i has offset bits b_d = (i >> d) & 1 (x fastest).
  *  - Coefficients per vertex and channel, in this order:
  *      3-D: f, g_x, g_y, g_z, H_xx, H_yy, H_zz, H_xy, H_xz, H_yz   (K = 1 / 4 / 10)
@@ -168,26 +170,28 @@ static int64_t vertex_index(int dim, int res, const int *cell, int i)
     return v;
 }
 
-/* Field value and spatial gradient (grid units) of every channel for a
- * given cell and local coordinate t (Eq. 3 + Eq. 4). */
+/* Field value and spatial gradient d f / d x (world units) of every channel
+ * for a given cell and local coordinate t (Eq. 3 + Eq. 4). The blend weights
+ * depend on t = x (res - 1) - cell, so d w / d x = (res - 1) d w / d t. */
 TGO_API void tgo_eval_cell(int dim, int res, int order, int C, const double *coefs,
-                           const int *cell, const double *t, double *f_out, double *gu_out)
+                           const int *cell, const double *t, double *f_out, double *gx_out)
 {
     int K = tgo_num_coefs(dim, order);
+    double h = 1.0 / (double)(res - 1);
     for (int ch = 0; ch < C; ++ch) {
-        double f = 0, gu[3] = {0, 0, 0};
+        double f = 0, gx[3] = {0, 0, 0};
         for (int i = 0; i < (1 << dim); ++i) {
             double delta[3] = {0, 0, 0}, dT[3];
-            for (int d = 0; d < dim; ++d) delta[d] = t[d] - (double)((i >> d) & 1);
+            for (int d = 0; d < dim; ++d) delta[d] = (t[d] - (double)((i >> d) & 1)) * h;   /* x - v_i */
             const double *th = coefs + (vertex_index(dim, res, cell, i) * C + ch) * K;
             double Ti = series_value(dim, order, th, delta);   /* Eq. 3 */
             series_gradient(dim, order, th, delta, dT);
             double w = corner_weight(dim, i, t);
             f += w * Ti;                                        /* Eq. 4 */
-            for (int a = 0; a < dim; ++a) gu[a] += corner_weight_grad(dim, i, t, a) * Ti + w * dT[a];
+            for (int a = 0; a < dim; ++a) gx[a] += corner_weight_grad(dim, i, t, a) / h * Ti + w * dT[a];
         }
         f_out[ch] = f;
-        if (gu_out) for (int a = 0; a < dim; ++a) gu_out[ch * dim + a] = gu[a];
+        if (gx_out) for (int a = 0; a < dim; ++a) gx_out[ch * dim + a] = gx[a];
     }
 }
 
@@ -198,10 +202,10 @@ TGO_API void tgo_query(int dim, int res, int order, int C, const double *coefs, 
 {
     #pragma omp parallel for schedule(static)
     for (int64_t n = 0; n < N; ++n) {
-        int cell[3]; double t[3], gu[16 * 3];
+        int cell[3]; double t[3], gx[16 * 3];
         tgo_locate(dim, res, pts + n * dim, cell, t);
-        tgo_eval_cell(dim, res, order, C, coefs, cell, t, out + n * C, gu);
-        if (grad_x) for (int j = 0; j < C * dim; ++j) grad_x[n * C * dim + j] = gu[j] * (double)(res - 1);
+        tgo_eval_cell(dim, res, order, C, coefs, cell, t, out + n * C, gx);
+        if (grad_x) for (int j = 0; j < C * dim; ++j) grad_x[n * C * dim + j] = gx[j];
         if (cells) for (int d = 0; d < dim; ++d) cells[n * dim + d] = cell[d];
         if (ts) for (int d = 0; d < dim; ++d) ts[n * dim + d] = t[d];
     }
@@ -210,7 +214,7 @@ TGO_API void tgo_query(int dim, int res, int order, int C, const double *coefs, 
 /* Coefficient gradient (direct grid optimisation, Sec. 3.1 / Sec. 3.3):
  * the field is linear in the coefficients, so dL/dtheta = J^T dL/df with
  * J_{n,(i,k)} = w_i(t) phi_k(delta_i), plus the same for the spatial gradient
- * with d/du of (w_i phi_k). Accumulates into coef_grad; abs_grad (optional)
+ * with d/dx of (w_i phi_k). Accumulates into coef_grad; abs_grad (optional)
  * accumulates the sum of the absolute values of the individual terms of each
  * contribution (the magnitude FP32 rounding of that sum is relative to), for
  * the scale-aware tolerance. */
@@ -219,18 +223,18 @@ TGO_API void tgo_query_backward(int dim, int res, int order, int C, int64_t N, c
                                 double *coef_grad, double *abs_grad)
 {
     int K = tgo_num_coefs(dim, order);
-    double hinv = (double)(res - 1);
+    double h = 1.0 / (double)(res - 1);
     #pragma omp parallel for schedule(static)
     for (int64_t n = 0; n < N; ++n) {
         int cell[3]; double t[3];
         tgo_locate(dim, res, pts + n * dim, cell, t);
         for (int i = 0; i < (1 << dim); ++i) {
             double delta[3] = {0, 0, 0}, phi[10], dphi[10][3];
-            for (int d = 0; d < dim; ++d) delta[d] = t[d] - (double)((i >> d) & 1);
+            for (int d = 0; d < dim; ++d) delta[d] = (t[d] - (double)((i >> d) & 1)) * h;
             series_jacobian(dim, order, delta, phi);
             series_jacobian_grad(dim, order, delta, dphi);
             double w = corner_weight(dim, i, t), dw[3];
-            for (int a = 0; a < dim; ++a) dw[a] = corner_weight_grad(dim, i, t, a);
+            for (int a = 0; a < dim; ++a) dw[a] = corner_weight_grad(dim, i, t, a) / h;   /* d w / d x */
             int64_t v = vertex_index(dim, res, cell, i);
             for (int ch = 0; ch < C; ++ch) {
                 for (int k = 0; k < K; ++k) {
@@ -238,7 +242,7 @@ TGO_API void tgo_query_backward(int dim, int res, int order, int C, int64_t N, c
                     double mag = fabs(c);   /* sum of |terms|: the scale FP32 rounding acts on */
                     if (dL_dgx)
                         for (int a = 0; a < dim; ++a) {
-                            double ga = hinv * dL_dgx[(n * C + ch) * dim + a];
+                            double ga = dL_dgx[(n * C + ch) * dim + a];
                             c += ga * (dw[a] * phi[k] + w * dphi[k][a]);
                             mag += fabs(ga) * (fabs(dw[a] * phi[k]) + fabs(w * dphi[k][a]));
                         }
@@ -269,7 +273,7 @@ TGO_API void tgo_query_absscale(int dim, int res, int order, int C, const double
             double s = 0;
             for (int i = 0; i < (1 << dim); ++i) {
                 double delta[3] = {0, 0, 0}, phi[10];
-                for (int d = 0; d < dim; ++d) delta[d] = t[d] - (double)((i >> d) & 1);
+                for (int d = 0; d < dim; ++d) delta[d] = (t[d] - (double)((i >> d) & 1)) / (double)(res - 1);
                 series_jacobian(dim, order, delta, phi);
                 const double *th = coefs + (vertex_index(dim, res, cell, i) * C + ch) * K;
                 double w = corner_weight(dim, i, t);

@@ -42,6 +42,10 @@ class GridInfo(ctypes.Structure):
                 ("coefs", _vp), ("master", _vp)]
 
 
+class ShapeStruct(ctypes.Structure):
+    _fields_ = [("n_spheres", _int), ("n_boxes", _int), ("spheres", _vp), ("boxes", _vp), ("area_cdf", _vp)]
+
+
 class AdamParams(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("step", _i64)]
@@ -67,6 +71,11 @@ _SIGS = {
     "tg_batch_timeouts": [_vp, ctypes.POINTER(_int)],
     "tg_query_noalloc": [_vp, _vp, _i64, _vp, _vp, _vp],
     "tg_adam_step": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
+    "tg_sdf_eval_target": [ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
+    "tg_sample_sdf_points": [ctypes.POINTER(ShapeStruct), ctypes.c_uint64, _i64, _i64, ctypes.c_float, _vp, _vp],
+    "tg_sdf_step": [_vp, _vp, ctypes.POINTER(ShapeStruct), _vp, _i64, ctypes.c_uint64, _i64, ctypes.c_float, _vp,
+                    _vp, _vp],
+    "tg_sdf_error": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
 }
 
 
@@ -301,3 +310,51 @@ def tg_adam_step(grid: Grid, coef_grad, lr: float, step: int, beta1=0.9, beta2=0
     prm = AdamParams(lr, beta1, beta2, eps, step)
     _check(load().tg_adam_step(grid.handle, _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), ctypes.byref(prm),
                                _stream(stream)), "tg_adam_step")
+
+
+class DeviceShape:
+    """A union of spheres (S, 4) and boxes (B, 6) in device memory, with its area CDF."""
+
+    def __init__(self, spheres, boxes, area_cdf=None, device="cuda"):
+        f = lambda a, w: torch.as_tensor(a, dtype=torch.float32).reshape(-1, w).contiguous().to(device)
+        self.spheres = f(spheres, 4)
+        self.boxes = f(boxes, 6)
+        self.cdf = None if area_cdf is None else torch.as_tensor(area_cdf, dtype=torch.float32).contiguous().to(device)
+        self.struct = ShapeStruct(self.spheres.shape[0], self.boxes.shape[0],
+                                  self.spheres.data_ptr() if self.spheres.numel() else None,
+                                  self.boxes.data_ptr() if self.boxes.numel() else None,
+                                  None if self.cdf is None else self.cdf.data_ptr())
+
+
+def tg_sdf_eval_target(shape: DeviceShape, pts, stream=None):
+    d = torch.empty(pts.shape[0], device=pts.device, dtype=torch.float32)
+    _check(load().tg_sdf_eval_target(ctypes.byref(shape.struct), _ptr(pts, "pts"), pts.shape[0], _ptr(d, "d"),
+                                     _stream(stream)), "tg_sdf_eval_target")
+    return d
+
+
+def tg_sample_sdf_points(shape: DeviceShape, seed: int, step: int, n: int, jitter: float = 0.01, out=None,
+                         stream=None):
+    if out is None:
+        out = torch.empty((n, 3), device="cuda", dtype=torch.float32)
+    _check(load().tg_sample_sdf_points(ctypes.byref(shape.struct), seed, step, n, jitter, _ptr(out, "pts", numel=3 * n),
+                                       _stream(stream)), "tg_sample_sdf_points")
+    return out
+
+
+def tg_sdf_step(grid: Grid, batch: Batch, shape: DeviceShape, coef_grad, loss_sums, pts=None, n=None, seed=0,
+                step=0, lambda_eik=0.0, stream=None):
+    n = pts.shape[0] if pts is not None else n
+    _check(load().tg_sdf_step(grid.handle, batch.handle, ctypes.byref(shape.struct),
+                              None if pts is None else _ptr(pts, "pts", numel=3 * n), n, seed, step, lambda_eik,
+                              _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), _ptr(loss_sums, "loss_sums", numel=2),
+                              _stream(stream)), "tg_sdf_step")
+    batch.n = n
+
+
+def tg_sdf_error(grid: Grid, shape: DeviceShape, pts, err_sum=None, stream=None):
+    if err_sum is None:
+        err_sum = torch.zeros(1, device="cuda", dtype=torch.float32)
+    _check(load().tg_sdf_error(grid.handle, ctypes.byref(shape.struct), _ptr(pts, "pts"), pts.shape[0],
+                               _ptr(err_sum, "err_sum"), _stream(stream)), "tg_sdf_error")
+    return err_sum

@@ -85,7 +85,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
             for (int ch = 0; ch < C; ++ch) v[3 + ch] = __ldg(dLdf + n * C + ch);
             if constexpr (HAS_G) {
 #pragma unroll
-                for (int j = 0; j < 3 * C; ++j) v[3 + C + j] = __ldg(dLdg + n * 3 * C + j) * scale;
+                for (int j = 0; j < 3 * C; ++j) v[3 + C + j] = __ldg(dLdg + n * 3 * C + j);
             }
 #pragma unroll
             for (int j = R::fields; j < RS; ++j) v[j] = 0.f;
@@ -94,7 +94,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
                 *reinterpret_cast<float4 *>(rec + pos * RS + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
         __syncthreads();
-        gather_round<ORDER, C, HAS_G, kBwdThreads, BXI>(rec, ints, tile);
+        gather_round<ORDER, C, HAS_G, kBwdThreads, BXI>(rec, ints, tile, scale);
         __syncthreads();
     }
 

@@ -75,7 +75,7 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
         return;
     }
 
-    const float scale = (float)(res - 1);
+    const float scale = (float)(res - 1), h = 1.0f / (float)(res - 1);
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const float4 q = sorted[p];
         const int64_t n = p;                       // binned-order output slot
@@ -83,7 +83,7 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
         int c[3];
         float t[3];
         locate<3>(x, res, scale, c, t);
-        const PointTables3<ORDER> P(t);
+        const PointTables3<ORDER> P(t, h);
         const T *cell = tile + ((c[2] - z0) * kBV + (c[1] - y0)) * BXI + (c[0] - x0) * NV;
         float f[C], gu[C][3];
 #pragma unroll
@@ -98,7 +98,10 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
             load_block_smem<T, NV>(cell + off, th);
             const float w = P.template weight<I>();
             float dw[3];
-            if constexpr (WANT_GRAD) P.template dweight<I>(dw);
+            if constexpr (WANT_GRAD) {
+                P.template dweight<I>(dw);
+                dw[0] *= scale; dw[1] *= scale; dw[2] *= scale;     // d w / d x
+            }
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
                 const float Tv = P.template value<I>(th + ch * K);       // Eq. 3
@@ -116,7 +119,7 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
             out[n * C + ch] = f[ch];
             if constexpr (WANT_GRAD) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) gx[(n * C + ch) * 3 + d] = gu[ch][d] * scale;
+                for (int d = 0; d < 3; ++d) gx[(n * C + ch) * 3 + d] = gu[ch][d];
             }
         }
     }

@@ -19,7 +19,7 @@ constexpr int kBrickVerts = kBV * kBV * kBV;   // 729
 constexpr int kMaxLoadBins = 64;               // vertex loads >= 63 share the last bin
 
 // Staged point record: t (3), s = dL/df (C) and, with a spatial-gradient
-// upstream, g = dL/d(grad_u f) in grid units (3 C); padded to 16 bytes.
+// upstream, g = dL/d(grad_x f) (3 C, world units); padded to 16 bytes.
 template <int C, bool HAS_G>
 struct GatherRec {
     static constexpr int fields = 3 + C + (HAS_G ? 3 * C : 0);
@@ -145,8 +145,9 @@ __device__ __forceinline__ void gather_order_vertices(int *ints)
 // Accumulates into acc[NV] the contributions of all staged points of the
 // incident cells of vertex v (local coordinates).
 template <int ORDER, int C, bool HAS_G>
-__device__ __forceinline__ void gather_vertex(int v, const float *rec, const int *off, float *acc)
+__device__ __forceinline__ void gather_vertex(int v, const float *rec, const int *off, float scale, float *acc)
 {
+    const float h = 1.0f / scale;
     constexpr int K = Basis<3, ORDER>::K;
     constexpr int RS = GatherRec<C, HAS_G>::stride;
     const int vx = v % kBV, vy = (v / kBV) % kBV, vz = v / (kBV * kBV);
@@ -181,16 +182,16 @@ __device__ __forceinline__ void gather_vertex(int v, const float *rec, const int
         const float a1 = by ? t1 : 1.f - t1;
         const float a2 = bz ? t2 : 1.f - t2;
         const float w = a0 * a1 * a2;
-        const float dl[3] = {bx ? t0 - 1.f : t0, by ? t1 - 1.f : t1, bz ? t2 - 1.f : t2};
+        const float dl[3] = {(bx ? t0 - 1.f : t0) * h, (by ? t1 - 1.f : t1) * h, (bz ? t2 - 1.f : t2) * h};
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) {
             float s = w * (ch == 0 ? tq.w : q[3 + ch]);
             float g[3];
             if constexpr (HAS_G) {
                 const float *gp = q + 3 + C + 3 * ch;
-                const float dw0 = (bx ? 1.f : -1.f) * a1 * a2;
-                const float dw1 = (by ? 1.f : -1.f) * a0 * a2;
-                const float dw2 = (bz ? 1.f : -1.f) * a0 * a1;
+                const float dw0 = (bx ? scale : -scale) * a1 * a2;     // d w / d x
+                const float dw1 = (by ? scale : -scale) * a0 * a2;
+                const float dw2 = (bz ? scale : -scale) * a0 * a1;
                 s = fmaf(dw0, gp[0], fmaf(dw1, gp[1], fmaf(dw2, gp[2], s)));
                 g[0] = w * gp[0]; g[1] = w * gp[1]; g[2] = w * gp[2];
             }
@@ -202,7 +203,7 @@ __device__ __forceinline__ void gather_vertex(int v, const float *rec, const int
 // One gather round: all NT threads take the vertices in load order and add
 // their sums into the shared tile (row stride BXI floats, vertex stride NV).
 template <int ORDER, int C, bool HAS_G, int NT, int BXI>
-__device__ __forceinline__ void gather_round(const float *rec, int *ints, float *tile)
+__device__ __forceinline__ void gather_round(const float *rec, int *ints, float *tile, float scale)
 {
     constexpr int NV = Basis<3, ORDER>::K * C;
     gather_order_vertices<NT>(ints);
@@ -212,7 +213,7 @@ __device__ __forceinline__ void gather_round(const float *rec, int *ints, float 
         float acc[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) acc[k] = 0.f;
-        gather_vertex<ORDER, C, HAS_G>(v, rec, off, acc);
+        gather_vertex<ORDER, C, HAS_G>(v, rec, off, scale, acc);
         float *d = tile + (v / kBV) * BXI + (v % kBV) * NV;
 #pragma unroll
         for (int k = 0; k < NV; ++k) d[k] += acc[k];

@@ -137,7 +137,8 @@ __device__ __forceinline__ void locate(const float *x, int res, float scale, int
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 1 / Eq. 3: the truncated series as a linear form in its coefficients.
+// Eq. 1 / Eq. 3: the truncated series as a linear form in its coefficients,
+// evaluated at the world offset delta = x - v_i.
 // phi[k] = dT/dtheta_k at delta; dphi[k][d] = d phi_k / d delta_d.
 // Basis order: 1, delta_d, delta_d^2 / 2, then delta_a delta_b for a < b in
 // the order (x,y), (x,z), (y,z).
@@ -295,25 +296,26 @@ __device__ __forceinline__ int64_t corner_offset(int i, int res)
 // ---------------------------------------------------------------------------
 // 3-D point tables: everything of Eq. 3 / Eq. 4 that depends on the point
 // but not on the corner's coefficients, computed once per point. For corner
-// bits b, delta_d = u[b_d][d]; the series basis is
+// bits b, delta_d = u[b_d][d] = (t_d - b_d) h is the world offset x - v_i
+// (h = 1 / (res - 1)); the series basis is
 //   1, u[b_d][d], h[b_d][d] = u^2 / 2, p_ab[b_a][b_b] = u[b_a][a] u[b_b][b]
 // and the blend weight is w = a[b_x][0] a[b_y][1] a[b_z][2], a[0] = 1 - t,
 // a[1] = t. T_i and its adjoint then cost one FMA per coefficient.
 // ---------------------------------------------------------------------------
 template <int ORDER>
 struct PointTables3 {
-    float u[2][3];            // delta components t - b
+    float u[2][3];            // delta components (t - b) h
     float h[2][3];            // delta^2 / 2
     float pxy[2][2], pxz[2][2], pyz[2][2];
     float a[2][3];            // weight factors
     float wxy[2][2];          // a_x a_y
 
-    __device__ __forceinline__ explicit PointTables3(const float *t)
+    __device__ __forceinline__ PointTables3(const float *t, float cell)
     {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            u[0][d] = t[d];
-            u[1][d] = t[d] - 1.0f;
+            u[0][d] = t[d] * cell;
+            u[1][d] = (t[d] - 1.0f) * cell;
             a[0][d] = 1.0f - t[d];
             a[1][d] = t[d];
             if (ORDER >= 2) {
@@ -340,7 +342,7 @@ struct PointTables3 {
         return wxy[I & 1][(I >> 1) & 1] * a[(I >> 2) & 1][2];
     }
 
-    // d w / d t_d for corner I.
+    // d w / d t_d for corner I (d w / d x_d = (res - 1) d w / d t_d).
     template <int I>
     __device__ __forceinline__ void dweight(float *dw) const
     {

@@ -18,7 +18,7 @@ query_fwd_kernel(const T *__restrict__ coefs, int res, const float *__restrict__
     using B = Basis<DIM, ORDER>;
     constexpr int K = B::K;
     constexpr int NV = K * C;
-    const float scale = (float)(res - 1);
+    const float scale = (float)(res - 1), h = 1.0f / (float)(res - 1);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += stride) {
         float x[DIM];
@@ -43,7 +43,10 @@ query_fwd_kernel(const T *__restrict__ coefs, int res, const float *__restrict__
             float dw[DIM], dl[DIM];
             const float w = corner_weight<DIM>(i, t, dw);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) dl[d] = t[d] - (float)((i >> d) & 1);
+            for (int d = 0; d < DIM; ++d) {
+                dl[d] = (t[d] - (float)((i >> d) & 1)) * h;          // x - v_i
+                dw[d] *= scale;                                      // d w / d x
+            }
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
                 float g[DIM];
@@ -58,7 +61,7 @@ query_fwd_kernel(const T *__restrict__ coefs, int res, const float *__restrict__
             out[n * C + ch] = f[ch];
             if (gx) {
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) gx[(n * C + ch) * DIM + d] = gu[ch][d] * scale;
+                for (int d = 0; d < DIM; ++d) gx[(n * C + ch) * DIM + d] = gu[ch][d];
             }
         }
     }
@@ -72,10 +75,11 @@ __device__ __forceinline__ void corner_contrib(int i, const float *t, float scal
 {
     using B = Basis<DIM, ORDER>;
     constexpr int K = B::K;
+    const float h = 1.0f / scale;
     float dw[DIM], dl[DIM];
     const float w = corner_weight<DIM>(i, t, dw);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) dl[d] = t[d] - (float)((i >> d) & 1);
+    for (int d = 0; d < DIM; ++d) dl[d] = (t[d] - (float)((i >> d) & 1)) * h;   // x - v_i
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) {
         float s = w * uf[ch];
@@ -85,8 +89,8 @@ __device__ __forceinline__ void corner_contrib(int i, const float *t, float scal
         if (has_g) {
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                const float gd = ug[ch][d] * scale;      // world -> grid units
-                s = fmaf(dw[d], gd, s);
+                const float gd = ug[ch][d];
+                s = fmaf(dw[d] * scale, gd, s);          // d w / d x = (res - 1) d w / d t
                 q[d] = w * gd;
             }
         }

@@ -82,7 +82,7 @@ def test_order0_equals_grid_sample(dim, res, C):
 # Polynomial reproduction (Eq. 1 + the partition of unity of Eq. 4)
 # --------------------------------------------------------------------------
 def taylor_data_of_poly(dim, res, order, p, grad, hess):
-    """Exact Taylor data (grid units) of a polynomial at every vertex, exchange layout."""
+    """Exact Taylor data (derivatives in x, Eq. 1) of a polynomial at every vertex, exchange layout."""
     h = 1.0 / (res - 1)
     K = W.n_coefs(dim, order)
     axes = np.meshgrid(*[np.arange(res) * h] * dim, indexing="ij")
@@ -93,9 +93,9 @@ def taylor_data_of_poly(dim, res, order, p, grad, hess):
     out = np.zeros((res ** dim, K))
     out[:, 0] = [p(c) for c in coords]
     if order >= 1:
-        out[:, 1:1 + dim] = np.array([grad(c) for c in coords]) * h
+        out[:, 1:1 + dim] = np.array([grad(c) for c in coords])
     if order >= 2:
-        Hs = np.array([hess(c) for c in coords]) * h * h
+        Hs = np.array([hess(c) for c in coords])
         diag = [Hs[:, a, a] for a in range(dim)]
         off = [Hs[:, 0, 1], Hs[:, 0, 2], Hs[:, 1, 2]] if dim == 3 else [Hs[:, 0, 1]]
         out[:, 1 + dim:] = np.stack(diag + off, 1)
@@ -173,14 +173,13 @@ def test_zero_derivatives_reduce_to_order0():
 
 
 def test_hessian_offdiagonal_order():
-    """A pure H_xz coefficient at every vertex gives the field x z h^{-2}-scaled cross term only."""
+    """The field x z stores its second derivative in the H_xz slot only (value 1 at every vertex)."""
     res = 3
-    h = 1.0 / (res - 1)
     p = lambda x: x[0] * x[2]
     coefs = taylor_data_of_poly(3, res, 2, p, lambda x: np.array([x[2], 0.0, x[0]]),
                                 lambda x: np.array([[0, 0, 1.0], [0, 0, 0], [1.0, 0, 0]]))
     c = coefs.reshape(-1, 10)
-    assert np.allclose(c[:, 8], h * h) and np.allclose(c[:, 7], 0) and np.allclose(c[:, 9], 0)
+    assert np.allclose(c[:, 8], 1.0) and np.allclose(c[:, 7], 0) and np.allclose(c[:, 9], 0)
     pts = rng(10).random((100, 3)).astype(np.float32)
     out, _, _, _ = oracle.query(3, res, 2, 1, coefs, pts, want_grad=False)
     np.testing.assert_allclose(out[:, 0], pts[:, 0].astype(np.float64) * pts[:, 2], atol=5e-6)
@@ -219,13 +218,14 @@ def test_spatial_gradient_finite_differences(dim, order):
     for _ in range(20):
         cell = r.integers(0, res - 1, size=dim)
         t = 0.1 + 0.8 * r.random(dim)
-        _, gu = oracle.eval_cell(dim, res, order, C, coefs, cell, t)
+        _, gx = oracle.eval_cell(dim, res, order, C, coefs, cell, t)
         for a in range(dim):
             tp = t.copy(); tp[a] += eps
             tm = t.copy(); tm[a] -= eps
             fp, _ = oracle.eval_cell(dim, res, order, C, coefs, cell, tp)
             fm, _ = oracle.eval_cell(dim, res, order, C, coefs, cell, tm)
-            np.testing.assert_allclose(gu[:, a], (fp - fm) / (2 * eps), atol=1e-8)
+            # x = (cell + t) h: d/dx = (res - 1) d/dt
+            np.testing.assert_allclose(gx[:, a], (fp - fm) / (2 * eps) * (res - 1), atol=1e-7)
 
 
 def test_query_gradient_is_world_units():
@@ -235,8 +235,8 @@ def test_query_gradient_is_world_units():
     pts = r.random((50, 3)).astype(np.float32)
     _, gx, cells, ts = oracle.query(3, res, 2, 1, coefs, pts, want_cells=True)
     for n in range(50):
-        _, gu = oracle.eval_cell(3, res, 2, 1, coefs, cells[n], ts[n])
-        np.testing.assert_allclose(gx[n, 0], gu[0] * (res - 1), rtol=1e-13, atol=1e-13)
+        _, gc = oracle.eval_cell(3, res, 2, 1, coefs, cells[n], ts[n])
+        np.testing.assert_allclose(gx[n, 0], gc[0], rtol=1e-13, atol=1e-13)
 
 
 # --------------------------------------------------------------------------
