@@ -290,6 +290,31 @@ TG_API tg_status tg_sdf_step(const tg_grid *grid, tg_batch *batch, const tg_shap
 TG_API tg_status tg_sdf_error(const tg_grid *grid, const tg_shape *shape, const float *pts, int64_t N,
                               float *err_sum, tg_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiable ray marching (Sec. 3.3, Eq. 9 - Eq. 11).
+ * ------------------------------------------------------------------------ */
+
+/* Renders R rays (rays_o, rays_d: device, R x 3, unit directions) through a
+ * density grid (3-D, 1 channel, sigma = softplus(f), Eq. 9) and a colour grid
+ * (3-D, 3 channels, c = sigmoid(f)) of the same res, with S (1..512)
+ * stratified samples per ray inside the unit cube:
+ *   t_i = near + (i + xi_i)(far - near)/S,  xi_i = U(seed, ray_base + r, i),
+ *   delta_i = t_{i+1} - t_i (t_S = far),
+ *   C(r) = sum_i T_i (1 - exp(-sigma_i delta_i)) c_i + T_S bg        (Eq. 10)
+ * with T_i = exp(-sum_{j<i} sigma_j delta_j); a ray that misses the cube is
+ * bg. Writes rgb_out (device, R x 3).
+ * Training (target_rgb != NULL, device R x 3): adds sum_r ||C - C*||^2 into
+ * loss_sum[0] (device; divide by R for the loss of Eq. 11) and ADDS the coefficient gradients of Eq. 11 into density_grad and
+ * color_grad (device, FP32, each grid's n_coefs). The per-sample derivatives
+ * come from the same pass; the samples are binned into `batch` (created for
+ * the grids' res with max_points >= R * S) and scattered by the binned
+ * backward. Both grids FP32 or both BF16; orders (2,1), (1,1), (2,0) or (0,0).
+ * The first training call may grow the batch's workspace (7 floats per sample). */
+TG_API tg_status tg_render_rays(const tg_grid *density, const tg_grid *color, const float *rays_o,
+                                const float *rays_d, int64_t R, int S, uint64_t seed, uint64_t ray_base,
+                                float bg, float *rgb_out, const float *target_rgb, tg_batch *batch,
+                                float *density_grad, float *color_grad, float *loss_sum, tg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,6 +61,7 @@ def lib():
             L.tgo_ray_box.argtypes = [_f64p, _f64p, _f64p, _f64p]; L.tgo_ray_box.restype = i32
             L.tgo_render.argtypes = [i32, i32, _f64p, i32, _f64p, i64, i32, _f32p, _f32p, u64, u64, f64,
                                      _f64p, _f32p, _f64p, _f64p, _f64p]
+            L.tgo_render_blobs.argtypes = [i32, _f64p, _f64p, _f64p, _f64p, i64, _f32p, _f32p, i32, f64, _f64p]
             _lib = L
     return _lib
 
@@ -183,3 +184,13 @@ def render(res, od, dcoef, oc, ccoef, rays_o, rays_d, S, seed, ray_base=0, bg=1.
     if target is None:
         return rgb
     return rgb, float(loss[0]), dg, cg
+
+
+def render_blobs(scene, rays_o, rays_d, n_samples=1024, bg=1.0):
+    """Ground-truth colours of the blob scene (mu, inv_cov, amp, rgb) along rays, (R, 3) float64."""
+    mu, icov, amp, rgb = (np.ascontiguousarray(a, np.float64) for a in scene)
+    rays_o = _c(rays_o, np.float32).reshape(-1, 3); rays_d = _c(rays_d, np.float32).reshape(-1, 3)
+    out = np.zeros((rays_o.shape[0], 3))
+    lib().tgo_render_blobs(mu.shape[0], _p(mu, _f64p), _p(icov, _f64p), _p(amp, _f64p), _p(rgb, _f64p),
+                           rays_o.shape[0], _p(rays_o, _f32p), _p(rays_d, _f32p), n_samples, bg, _p(out, _f64p))
+    return out

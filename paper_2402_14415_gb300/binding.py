@@ -76,6 +76,8 @@ _SIGS = {
     "tg_sdf_step": [_vp, _vp, ctypes.POINTER(ShapeStruct), _vp, _i64, ctypes.c_uint64, _i64, ctypes.c_float, _vp,
                     _vp, _vp],
     "tg_sdf_error": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
+    "tg_render_rays": [_vp, _vp, _vp, _vp, _i64, _int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_float, _vp, _vp,
+                       _vp, _vp, _vp, _vp, _vp],
 }
 
 
@@ -358,3 +360,22 @@ def tg_sdf_error(grid: Grid, shape: DeviceShape, pts, err_sum=None, stream=None)
     _check(load().tg_sdf_error(grid.handle, ctypes.byref(shape.struct), _ptr(pts, "pts"), pts.shape[0],
                                _ptr(err_sum, "err_sum"), _stream(stream)), "tg_sdf_error")
     return err_sum
+
+
+def tg_render_rays(density: Grid, color: Grid, rays_o, rays_d, S: int, seed: int = 0, ray_base: int = 0,
+                   bg: float = 1.0, target=None, batch: Batch | None = None, density_grad=None, color_grad=None,
+                   loss_sum=None, out=None, stream=None):
+    """Eq. 10 rendering; with `target` also the Eq. 11 loss and both coefficient gradients."""
+    R = rays_o.shape[0]
+    if out is None:
+        out = torch.empty((R, 3), device=rays_o.device, dtype=torch.float32)
+    _check(load().tg_render_rays(density.handle, color.handle, _ptr(rays_o, "rays_o", numel=3 * R),
+                                 _ptr(rays_d, "rays_d", numel=3 * R), R, S, seed, ray_base, bg,
+                                 _ptr(out, "out", numel=3 * R), _ptr(target, "target", numel=3 * R, optional=True),
+                                 None if batch is None else batch.handle,
+                                 _ptr(density_grad, "density_grad", optional=True),
+                                 _ptr(color_grad, "color_grad", optional=True),
+                                 _ptr(loss_sum, "loss_sum", optional=True), _stream(stream)), "tg_render_rays")
+    if batch is not None and target is not None:
+        batch.n = R * S
+    return out

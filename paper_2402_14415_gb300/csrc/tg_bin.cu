@@ -398,6 +398,21 @@ tg_status ensure_stage(tg_batch *bt, int64_t floats, const char *who)
     return TG_OK;
 }
 
+tg_status ensure_aux(tg_batch *bt, int64_t floats, const char *who)
+{
+    if (bt->aux_floats >= floats) return TG_OK;
+    float *p = nullptr;
+    tg_status st = cuda_status(cudaMalloc(&p, (size_t)floats * sizeof(float)), who);
+    if (st != TG_OK) return st;
+    if (bt->aux) {
+        cudaDeviceSynchronize();
+        cudaFree(bt->aux);
+    }
+    bt->aux = p;
+    bt->aux_floats = floats;
+    return TG_OK;
+}
+
 tg_status unpermute_outputs(const tg_batch *bt, int C, float *out, float *grad_x, cudaStream_t s)
 {
     unpermute_kernel<<<grid_for((const void *)unpermute_kernel, 256, bt->n), 256, 0, s>>>(bt->perm, bt->stage, bt->n,
@@ -470,6 +485,7 @@ tg_status tg_batch_destroy(tg_batch *b)
     cudaFree(b->coarse);
     cudaFree(b->perm);
     if (b->stage_owned) cudaFree(b->stage);
+    cudaFree(b->aux);
     cudaFree(b->status);
     free(b);
     return TG_OK;

@@ -23,6 +23,8 @@ struct tg_batch {
     float *stage;         // binned-order staging of outputs / upstream gradients
     int64_t stage_floats; // capacity of stage
     bool stage_owned;     // stage was allocated by the batch (false: caller-provided scratch)
+    float *aux;           // per-sample workspace of the renderer (grown on demand)
+    int64_t aux_floats;
     int *status;          // device word: non-zero after a bounded wait gave up
     int device;
 };
@@ -61,6 +63,7 @@ tg_status check_pair(const tg_grid *g, const tg_batch *bt, const char *who);
 // Makes bt->stage hold at least `floats` floats (grows a batch-owned buffer
 // synchronously; a caller-provided buffer that is too small is an error).
 tg_status ensure_stage(tg_batch *bt, int64_t floats, const char *who);
+tg_status ensure_aux(tg_batch *bt, int64_t floats, const char *who);
 
 // out[perm[p]] = stage[p] (and the spatial-gradient block that follows it).
 tg_status unpermute_outputs(const tg_batch *bt, int C, float *out, float *grad_x, cudaStream_t s);

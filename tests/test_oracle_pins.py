@@ -440,3 +440,16 @@ def test_render_gradient_finite_differences():
         e = np.zeros_like(cco); e[j] = eps
         fd = (L(dco, cco + e) - L(dco, cco - e)) / (2 * eps)
         assert abs(fd - cg[j]) < 1e-7 + 1e-5 * abs(fd), ("colour", j, fd, cg[j])
+
+
+def test_blob_scene_renderer_limits():
+    """A dense blob saturates to its colour; a ray that misses the cube renders bg; an empty scene is bg."""
+    mu = np.array([[0.5, 0.5, 0.5]]); icov = np.eye(3)[None] / 0.05 ** 2
+    amp = np.array([5000.0]); rgb = np.array([[0.2, 0.4, 0.8]])
+    o = np.array([[-1.0, 0.5, 0.5], [2.0, 2.0, 2.0]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]], np.float32)
+    c = oracle.render_blobs((mu, icov, amp, rgb), o, d, n_samples=4096, bg=1.0)
+    np.testing.assert_allclose(c[0], rgb[0], atol=1e-3)
+    np.testing.assert_allclose(c[1], [1, 1, 1])
+    c0 = oracle.render_blobs((mu, icov, np.array([0.0]), rgb), o, d, n_samples=64, bg=0.25)
+    np.testing.assert_allclose(c0, 0.25)
