@@ -315,6 +315,80 @@ TG_API tg_status tg_render_rays(const tg_grid *density, const tg_grid *color, co
                                 float bg, float *rgb_out, const float *target_rgb, tg_batch *batch,
                                 float *density_grad, float *color_grad, float *loss_sum, tg_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Fit / query server (continuous batching; no paper counterpart - the paper
+ * fits one shape at a time). Fit jobs (Sec. 3.2 SDF fits) and query requests
+ * arrive at any time. A tick (tg_server_step) retires finished work, admits
+ * queued jobs while the sum of their device bytes stays within the budget,
+ * and launches one training step of every running fit job on that job's own
+ * stream - a CUDA graph captured at admission (sampler, binning, forward,
+ * loss, backward, Adam, a device-gated evaluation every eval_every steps)
+ * whose step counter, error and stop flag live in device memory - so the
+ * steps of all running jobs overlap on the GPU. The host never waits for the
+ * device inside a tick: progress is read from pinned status words.
+ * A finished fit job's grid stays resident (for queries) until tg_release.
+ * ------------------------------------------------------------------------ */
+typedef struct tg_server tg_server;
+typedef int64_t tg_job_id;
+
+typedef struct {
+    int res, order;
+    tg_dtype dtype;
+    uint64_t seed;              /* sampler seed of the fit batches; evaluation points use seed + 1 */
+    int n_spheres, n_boxes;     /* the target shape (host arrays, copied at submission) */
+    const float *spheres;       /* (host) n_spheres x 4 */
+    const float *boxes;         /* (host) n_boxes x 6 */
+    const float *area_cdf;      /* (host) n_spheres + n_boxes */
+    int64_t points_per_step;    /* fit batch size */
+    int64_t eval_points;        /* evaluation points (fixed per job) */
+    int eval_every;             /* evaluate the mean |SDF error| every this many steps */
+    int max_steps;
+    float tol;                  /* stop once the evaluated mean |SDF error| < tol */
+    float lr, lambda_eik, init_std;
+} tg_fit_desc;
+
+typedef enum { TG_JOB_QUEUED = 0, TG_JOB_RUNNING = 1, TG_JOB_DONE = 2, TG_JOB_FAILED = 3 } tg_job_state;
+
+typedef struct {
+    int state;                  /* tg_job_state */
+    int kind;                   /* 0 = fit, 1 = query */
+    int64_t steps;              /* fit steps done */
+    float error;                /* last evaluated mean |SDF error| (fit) */
+    double t_submit, t_start, t_done;   /* seconds on the server's monotonic clock */
+    int64_t points;             /* points processed (fit: steps x batch; query: N) */
+    size_t bytes;               /* device bytes charged to the budget */
+} tg_job_result;
+
+/* budget_bytes: HBM admission budget; max_running: at most this many fit
+ * jobs train at once (further admitted jobs wait in the queue). */
+TG_API tg_status tg_server_create(size_t budget_bytes, int max_running, tg_server **out);
+/* Waits for all device work of the server, then frees every job. */
+TG_API tg_status tg_server_destroy(tg_server *server);
+
+/* Enqueue a fit job. TG_EBUDGET if the job alone needs more than the budget;
+ * TG_EINVAL for a bad description. The job id is returned in *id. */
+TG_API tg_status tg_fit_job(tg_server *server, const tg_fit_desc *desc, tg_job_id *id);
+
+/* Enqueue a query of N points (device, N x 3) against the grid of fit job
+ * `grid_job` (queued, running or done but not released); out (device, N).
+ * The query runs on the fit job's stream, between two of its steps. */
+TG_API tg_status tg_query_job(tg_server *server, tg_job_id grid_job, const float *pts, int64_t N, float *out,
+                              tg_job_id *id);
+
+/* One tick (see above). *pending (optional) = jobs queued or running. */
+TG_API tg_status tg_server_step(tg_server *server, int *pending);
+
+TG_API tg_status tg_poll(tg_server *server, tg_job_id id, tg_job_result *result);
+
+/* The grid of a fit job (borrowed; valid until tg_release). */
+TG_API tg_status tg_server_grid(tg_server *server, tg_job_id id, tg_grid **grid);
+
+/* Frees a finished fit job's grid (or a finished query's record). TG_EBUSY if it is still running. */
+TG_API tg_status tg_release(tg_server *server, tg_job_id id);
+
+/* Seconds on the server's monotonic clock (the clock of tg_job_result). */
+TG_API double tg_server_time(const tg_server *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,20 @@ class ShapeStruct(ctypes.Structure):
     _fields_ = [("n_spheres", _int), ("n_boxes", _int), ("spheres", _vp), ("boxes", _vp), ("area_cdf", _vp)]
 
 
+class FitDesc(ctypes.Structure):
+    _fields_ = [("res", _int), ("order", _int), ("dtype", _int), ("seed", ctypes.c_uint64),
+                ("n_spheres", _int), ("n_boxes", _int), ("spheres", _vp), ("boxes", _vp), ("area_cdf", _vp),
+                ("points_per_step", _i64), ("eval_points", _i64), ("eval_every", _int), ("max_steps", _int),
+                ("tol", ctypes.c_float), ("lr", ctypes.c_float), ("lambda_eik", ctypes.c_float),
+                ("init_std", ctypes.c_float)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("state", _int), ("kind", _int), ("steps", _i64), ("error", ctypes.c_float),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("points", _i64), ("bytes", ctypes.c_size_t)]
+
+
 class AdamParams(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("step", _i64)]
@@ -76,13 +90,21 @@ _SIGS = {
     "tg_sdf_step": [_vp, _vp, ctypes.POINTER(ShapeStruct), _vp, _i64, ctypes.c_uint64, _i64, ctypes.c_float, _vp,
                     _vp, _vp],
     "tg_sdf_error": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
+    "tg_server_create": [ctypes.c_size_t, _int, ctypes.POINTER(_vp)],
+    "tg_server_destroy": [_vp],
+    "tg_fit_job": [_vp, ctypes.POINTER(FitDesc), ctypes.POINTER(_i64)],
+    "tg_query_job": [_vp, _i64, _vp, _i64, _vp, ctypes.POINTER(_i64)],
+    "tg_server_step": [_vp, ctypes.POINTER(_int)],
+    "tg_poll": [_vp, _i64, ctypes.POINTER(JobResult)],
+    "tg_server_grid": [_vp, _i64, ctypes.POINTER(_vp)],
+    "tg_release": [_vp, _i64],
     "tg_render_rays": [_vp, _vp, _vp, _vp, _i64, _int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_float, _vp, _vp,
                        _vp, _vp, _vp, _vp, _vp],
 }
 
 
 def exported_symbols() -> list[str]:
-    return list(_SIGS) + ["tg_status_string", "tg_last_error"]
+    return list(_SIGS) + ["tg_status_string", "tg_last_error", "tg_server_time"]
 
 
 def load():
@@ -100,6 +122,7 @@ def load():
             fn.restype = _int
         L.tg_status_string.argtypes = [_int]; L.tg_status_string.restype = ctypes.c_char_p
         L.tg_last_error.argtypes = []; L.tg_last_error.restype = ctypes.c_char_p
+        L.tg_server_time.argtypes = [_vp]; L.tg_server_time.restype = ctypes.c_double
         _lib = L
         return L
 
@@ -379,3 +402,81 @@ def tg_render_rays(density: Grid, color: Grid, rays_o, rays_d, S: int, seed: int
     if batch is not None and target is not None:
         batch.n = R * S
     return out
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
+class Server:
+    """Continuous-batching fit / query server (tg_server_*)."""
+
+    def __init__(self, budget_bytes: int, max_running: int = 64):
+        h = _vp()
+        _check(load().tg_server_create(budget_bytes, max_running, ctypes.byref(h)), "tg_server_create")
+        self._h = h.value
+        self._keep = {}
+
+    def fit_job(self, shape_spheres, shape_boxes, area_cdf, res, order=2, dtype="f32", seed=0, points_per_step=1 << 16,
+                eval_points=1 << 16, eval_every=10, max_steps=1000, tol=2e-3, lr=5e-3, lambda_eik=0.0,
+                init_std=1e-3) -> int:
+        import numpy as np
+        sph = np.ascontiguousarray(shape_spheres, np.float32).reshape(-1)
+        box = np.ascontiguousarray(shape_boxes, np.float32).reshape(-1)
+        cdf = np.ascontiguousarray(area_cdf, np.float32).reshape(-1)
+        d = FitDesc(res, order, DTYPES[dtype] if isinstance(dtype, str) else dtype, seed, sph.size // 4, box.size // 6,
+                    sph.ctypes.data if sph.size else None, box.ctypes.data if box.size else None, cdf.ctypes.data,
+                    points_per_step, eval_points, eval_every, max_steps, tol, lr, lambda_eik, init_std)
+        jid = _i64()
+        _check(load().tg_fit_job(self._h, ctypes.byref(d), ctypes.byref(jid)), "tg_fit_job")
+        return jid.value
+
+    def query_job(self, grid_job: int, pts: torch.Tensor, out: torch.Tensor) -> int:
+        jid = _i64()
+        _check(load().tg_query_job(self._h, grid_job, _ptr(pts, "pts"), pts.shape[0], _ptr(out, "out"),
+                                   ctypes.byref(jid)), "tg_query_job")
+        self._keep[jid.value] = (pts, out)
+        return jid.value
+
+    def step(self) -> int:
+        p = _int()
+        _check(load().tg_server_step(self._h, ctypes.byref(p)), "tg_server_step")
+        return p.value
+
+    def poll(self, jid: int) -> dict:
+        r = JobResult()
+        _check(load().tg_poll(self._h, jid, ctypes.byref(r)), "tg_poll")
+        return {"state": JOB_STATES.get(r.state, r.state), "kind": "fit" if r.kind == 0 else "query",
+                "steps": r.steps, "error": r.error, "t_submit": r.t_submit, "t_start": r.t_start,
+                "t_done": r.t_done, "points": r.points, "bytes": r.bytes}
+
+    def grid_coefs(self, jid: int, which: int = 1) -> torch.Tensor:
+        h = _vp()
+        _check(load().tg_server_grid(self._h, jid, ctypes.byref(h)), "tg_server_grid")
+        info = GridInfo()
+        _check(load().tg_get_info(h.value, ctypes.byref(info)), "tg_get_info")
+        out = torch.empty(info.n_coefs, device="cuda", dtype=torch.float32)
+        _check(load().tg_get_coefs(h.value, out.data_ptr(), which, _stream(None)), "tg_get_coefs")
+        return out
+
+    def release(self, jid: int):
+        _check(load().tg_release(self._h, jid), "tg_release")
+        self._keep.pop(jid, None)
+
+    def time(self) -> float:
+        return load().tg_server_time(self._h)
+
+    def run_until_idle(self, timeout_s: float = 600.0, sleep_s: float = 0.0):
+        import time
+        t0 = time.time()
+        while self.step() > 0:
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+            if sleep_s:
+                time.sleep(sleep_s)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tg_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close

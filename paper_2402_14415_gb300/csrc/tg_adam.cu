@@ -48,8 +48,13 @@ __device__ __forceinline__ void store4<__half>(__half *dst, int64_t j, float a, 
 template <typename T>
 __global__ void __launch_bounds__(256)
 adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
-            T *__restrict__ shadow, int64_t n, AdamCoef a)
+            T *__restrict__ shadow, int64_t n, AdamCoef a, const int64_t *__restrict__ step_dev, float lr)
 {
+    if (step_dev) {   // bias corrections of the 1-based step *step_dev + 1, read on the device
+        const float t = (float)(*step_dev + 1);
+        a.step_size = lr / (1.0f - powf(a.beta1, t));
+        a.inv_sqrt_bc2 = rsqrtf(1.0f - powf(a.beta2, t));
+    }
     const int64_t n4 = n >> 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     float4 *p4 = reinterpret_cast<float4 *>(p);
@@ -82,28 +87,32 @@ adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
 
 using namespace tg;
 
-extern "C" tg_status tg_adam_step(tg_grid *g, float *grad, const tg_adam *prm, tg_stream stream)
+namespace tg {
+
+tg_status ensure_adam_state(tg_grid *g)
 {
-    if (!g || !grad || !prm) return fail(TG_EINVAL, "tg_adam_step: NULL argument");
-    if (prm->step < 1) return fail(TG_EINVAL, "tg_adam_step: step must be >= 1");
-    if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
-        return fail(TG_EINVAL, "tg_adam_step: betas must lie in [0,1) and eps >= 0");
-    if (((uintptr_t)grad & 15) != 0) return fail(TG_EINVAL, "tg_adam_step: coef_grad must be 16-byte aligned");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!g->adam_m) {
-        tg_status st = cuda_status(cudaMalloc(&g->adam_m, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(m)");
-        if (st == TG_OK) st = cuda_status(cudaMalloc(&g->adam_v, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(v)");
-        if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_m, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero m");
-        if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_v, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero v");
-        if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_adam_step: init moments");
-        if (st != TG_OK) {
-            cudaFree(g->adam_m); cudaFree(g->adam_v);
-            g->adam_m = g->adam_v = nullptr;
-            return st;
-        }
+    if (g->adam_m) return TG_OK;
+    tg_status st = cuda_status(cudaMalloc(&g->adam_m, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(m)");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&g->adam_v, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(v)");
+    if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_m, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero m");
+    if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_v, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero v");
+    if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_adam_step: init moments");
+    if (st != TG_OK) {
+        cudaFree(g->adam_m); cudaFree(g->adam_v);
+        g->adam_m = g->adam_v = nullptr;
     }
-    const double b1t = 1.0 - pow((double)prm->beta1, (double)prm->step);
-    const double b2t = 1.0 - pow((double)prm->beta2, (double)prm->step);
+    return st;
+}
+
+// Adam over all coefficients; with step_dev the 0-based step index is read on
+// the device (for replayable CUDA graphs) and prm->step is ignored.
+tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t *step_dev, cudaStream_t s)
+{
+    tg_status st = ensure_adam_state(g);
+    if (st != TG_OK) return st;
+    const double step = step_dev ? 1.0 : (double)prm->step;
+    const double b1t = 1.0 - pow((double)prm->beta1, step);
+    const double b2t = 1.0 - pow((double)prm->beta2, step);
     AdamCoef a;
     a.beta1 = prm->beta1; a.beta2 = prm->beta2;
     a.one_m_b1 = 1.0f - prm->beta1; a.one_m_b2 = 1.0f - prm->beta2;
@@ -116,11 +125,25 @@ extern "C" tg_status tg_adam_step(tg_grid *g, float *grad, const tg_adam *prm, t
     int64_t cap = (int64_t)num_sms() * per_sm;
     unsigned nb = (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
     if (g->dtype == TG_F32)
-        adam_kernel<float><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, nullptr, g->ncoef, a);
+        adam_kernel<float><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, nullptr, g->ncoef, a, step_dev,
+                                              prm->lr);
     else if (g->dtype == TG_BF16)
         adam_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v,
-                                                      (__nv_bfloat16 *)g->store, g->ncoef, a);
+                                                      (__nv_bfloat16 *)g->store, g->ncoef, a, step_dev, prm->lr);
     else
-        adam_kernel<__half><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, (__half *)g->store, g->ncoef, a);
+        adam_kernel<__half><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, (__half *)g->store, g->ncoef, a,
+                                               step_dev, prm->lr);
     return launch_status("tg_adam_step");
+}
+
+}  // namespace tg
+
+extern "C" tg_status tg_adam_step(tg_grid *g, float *grad, const tg_adam *prm, tg_stream stream)
+{
+    if (!g || !grad || !prm) return fail(TG_EINVAL, "tg_adam_step: NULL argument");
+    if (prm->step < 1) return fail(TG_EINVAL, "tg_adam_step: step must be >= 1");
+    if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
+        return fail(TG_EINVAL, "tg_adam_step: betas must lie in [0,1) and eps >= 0");
+    if (((uintptr_t)grad & 15) != 0) return fail(TG_EINVAL, "tg_adam_step: coef_grad must be 16-byte aligned");
+    return adam_launch(g, grad, prm, nullptr, (cudaStream_t)stream);
 }

@@ -35,6 +35,11 @@ int num_sms();                      // SM count of the current device (cached pe
 // Resident blocks per SM of a kernel at a launch shape (cached per device and kernel).
 int blocks_per_sm(const void *kernel, int threads, size_t smem);
 
+// Adam over all coefficients (tg_adam.cu); with step_dev != nullptr the
+// 0-based step index is read on the device and prm->step is ignored.
+tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t *step_dev, cudaStream_t s);
+tg_status ensure_adam_state(tg_grid *g);
+
 inline int num_coefs(int dim, int order)
 {
     return 1 + (order >= 1 ? dim : 0) + (order >= 2 ? dim * (dim + 1) / 2 : 0);

@@ -2,16 +2,11 @@
 // batches, the per-point loss (Eq. 6 with w = 1, eikonal term of Eq. 8) and
 // the fitting step that composes binning, the binned forward with spatial
 // gradients, the loss and the binned backward - all in binned order.
-#include "tg_binned.cuh"
+#include "tg_sdf.cuh"
 
 namespace tg {
 
-struct ShapeView {
-    int ns, nb;
-    const float *sph, *box, *cdf;
-};
-
-static tg_status shape_view(const tg_shape *s, ShapeView *v, const char *who)
+tg_status shape_view(const tg_shape *s, ShapeView *v, const char *who)
 {
     if (!s) return fail(TG_EINVAL, "%s: shape is NULL", who);
     if (s->n_spheres < 0 || s->n_boxes < 0 || s->n_spheres + s->n_boxes < 1 || s->n_spheres + s->n_boxes > 1024)
@@ -87,10 +82,11 @@ __device__ __forceinline__ void surface_candidate(const ShapeView &s, float u0, 
     }
 }
 
-__global__ void sdf_sample_kernel(ShapeView s, uint64_t seed, int64_t step, int64_t N, float jitter,
-                                  float *__restrict__ pts)
+__global__ void sdf_sample_kernel(ShapeView s, uint64_t seed, int64_t step, const int64_t *__restrict__ step_dev,
+                                  int64_t N, float jitter, float *__restrict__ pts)
 {
     constexpr uint64_t SLOTS = 16;
+    if (step_dev) step = *step_dev;
     const int64_t n_uni = N / 2;
     const uint64_t base = (uint64_t)step * 256ull;
     const uint64_t key_u = stream_key(seed, base + 255ull);
@@ -170,8 +166,9 @@ sdf_loss_kernel(ShapeView s, const float4 *__restrict__ sorted, int64_t N, const
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256)
 sdf_error_kernel(ShapeView s, const T *__restrict__ coefs, int res, const float *__restrict__ pts, int64_t N,
-                 float *__restrict__ err)
+                 float *__restrict__ err, const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;
     __shared__ float tmp[32];
     constexpr int K = Basis<3, ORDER>::K;
     const float scale = (float)(res - 1);
@@ -202,6 +199,44 @@ static unsigned blocks_for(int64_t n, int per_sm = 8)
     return (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
 }
 
+tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, const float *pts, int64_t N,
+                        uint64_t seed, int64_t step, const int64_t *step_dev, float lambda_eik, float *coef_grad,
+                        float *loss_sums, cudaStream_t cs)
+{
+    tg_status st;
+    if ((st = ensure_stage(bt, 11 * N, "tg_sdf_step")) != TG_OK) return st;
+    float *f = bt->stage, *gx = bt->stage + N, *uf = bt->stage + 4 * N, *ug = bt->stage + 5 * N;
+    float *sampled = bt->stage + 8 * N;
+    const bool eik = lambda_eik > 0.f;
+    if (!pts) {
+        sdf_sample_kernel<<<blocks_for(N), 256, 0, cs>>>(s, seed, step, step_dev, N, 0.01f, sampled);
+        if ((st = launch_status("tg_sdf_step: sample")) != TG_OK) return st;
+        pts = sampled;
+    }
+    if ((st = tg_batch_bin(bt, pts, N, cs)) != TG_OK) return st;
+    if ((st = tg_query_binned(g, bt, f, eik ? gx : nullptr, TG_ORDER_BINNED, cs)) != TG_OK) return st;
+    sdf_loss_kernel<<<blocks_for(N), 256, 0, cs>>>(s, bt->sorted, N, f, eik ? gx : nullptr, lambda_eik,
+                                                   1.0f / (float)N, uf, ug, loss_sums);
+    if ((st = launch_status("tg_sdf_step: loss")) != TG_OK) return st;
+    return tg_query_backward_binned(g, bt, uf, eik ? ug : nullptr, coef_grad, TG_ORDER_BINNED, cs);
+}
+
+tg_status sdf_error_impl(const tg_grid *g, const ShapeView &s, const float *pts, int64_t N, float *err_sum,
+                         const int *gate, cudaStream_t cs)
+{
+    const unsigned nb = blocks_for(N);
+#define TG_ERR(T, O) sdf_error_kernel<T, O><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, pts, N, err_sum, gate)
+    if (g->dtype == TG_F32) {
+        if (g->order == 0) TG_ERR(float, 0); else if (g->order == 1) TG_ERR(float, 1); else TG_ERR(float, 2);
+    } else if (g->dtype == TG_BF16) {
+        if (g->order == 0) TG_ERR(__nv_bfloat16, 0); else if (g->order == 1) TG_ERR(__nv_bfloat16, 1); else TG_ERR(__nv_bfloat16, 2);
+    } else {
+        if (g->order == 0) TG_ERR(__half, 0); else if (g->order == 1) TG_ERR(__half, 1); else TG_ERR(__half, 2);
+    }
+#undef TG_ERR
+    return launch_status("tg_sdf_error");
+}
+
 }  // namespace tg
 
 using namespace tg;
@@ -230,7 +265,7 @@ tg_status tg_sample_sdf_points(const tg_shape *shape, uint64_t seed, int64_t ste
     if (N < 0 || step < 0) return fail(TG_EINVAL, "tg_sample_sdf_points: N and step must be >= 0");
     if (N == 0) return TG_OK;
     if (!pts) return fail(TG_EINVAL, "tg_sample_sdf_points: pts is NULL");
-    sdf_sample_kernel<<<blocks_for(N), 256, 0, (cudaStream_t)stream>>>(s, seed, step, N, jitter, pts);
+    sdf_sample_kernel<<<blocks_for(N), 256, 0, (cudaStream_t)stream>>>(s, seed, step, nullptr, N, jitter, pts);
     return launch_status("tg_sample_sdf_points");
 }
 
@@ -247,22 +282,7 @@ tg_status tg_sdf_step(const tg_grid *g, tg_batch *bt, const tg_shape *shape, con
     if (!coef_grad || !loss_sums) return fail(TG_EINVAL, "tg_sdf_step: NULL coef_grad or loss_sums");
     if (!pts && !s.cdf) return fail(TG_EINVAL, "tg_sdf_step: sampling needs area_cdf");
     if (!(lambda_eik >= 0.f)) return fail(TG_EINVAL, "tg_sdf_step: lambda_eik must be >= 0");
-    cudaStream_t cs = (cudaStream_t)stream;
-    if ((st = ensure_stage(bt, 11 * N, "tg_sdf_step")) != TG_OK) return st;
-    float *f = bt->stage, *gx = bt->stage + N, *uf = bt->stage + 4 * N, *ug = bt->stage + 5 * N;
-    float *sampled = bt->stage + 8 * N;
-    const bool eik = lambda_eik > 0.f;
-    if (!pts) {
-        sdf_sample_kernel<<<blocks_for(N), 256, 0, cs>>>(s, seed, step, N, 0.01f, sampled);
-        if ((st = launch_status("tg_sdf_step: sample")) != TG_OK) return st;
-        pts = sampled;
-    }
-    if ((st = tg_batch_bin(bt, pts, N, stream)) != TG_OK) return st;
-    if ((st = tg_query_binned(g, bt, f, eik ? gx : nullptr, TG_ORDER_BINNED, stream)) != TG_OK) return st;
-    sdf_loss_kernel<<<blocks_for(N), 256, 0, cs>>>(s, bt->sorted, N, f, eik ? gx : nullptr, lambda_eik,
-                                                   1.0f / (float)N, uf, ug, loss_sums);
-    if ((st = launch_status("tg_sdf_step: loss")) != TG_OK) return st;
-    return tg_query_backward_binned(g, bt, uf, eik ? ug : nullptr, coef_grad, TG_ORDER_BINNED, stream);
+    return sdf_step_impl(g, bt, s, pts, N, seed, step, nullptr, lambda_eik, coef_grad, loss_sums, (cudaStream_t)stream);
 }
 
 tg_status tg_sdf_error(const tg_grid *g, const tg_shape *shape, const float *pts, int64_t N, float *err_sum,
@@ -275,18 +295,7 @@ tg_status tg_sdf_error(const tg_grid *g, const tg_shape *shape, const float *pts
     if (N < 0) return fail(TG_EINVAL, "tg_sdf_error: N < 0");
     if (N == 0) return TG_OK;
     if (!pts || !err_sum) return fail(TG_EINVAL, "tg_sdf_error: NULL pts or err_sum");
-    cudaStream_t cs = (cudaStream_t)stream;
-    const unsigned nb = blocks_for(N);
-#define TG_ERR(T, O) sdf_error_kernel<T, O><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, pts, N, err_sum)
-    if (g->dtype == TG_F32) {
-        if (g->order == 0) TG_ERR(float, 0); else if (g->order == 1) TG_ERR(float, 1); else TG_ERR(float, 2);
-    } else if (g->dtype == TG_BF16) {
-        if (g->order == 0) TG_ERR(__nv_bfloat16, 0); else if (g->order == 1) TG_ERR(__nv_bfloat16, 1); else TG_ERR(__nv_bfloat16, 2);
-    } else {
-        if (g->order == 0) TG_ERR(__half, 0); else if (g->order == 1) TG_ERR(__half, 1); else TG_ERR(__half, 2);
-    }
-#undef TG_ERR
-    return launch_status("tg_sdf_error");
+    return sdf_error_impl(g, s, pts, N, err_sum, nullptr, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,433 @@
+// Continuous-batching fit / query server.
+//
+// Every admitted fit job owns a stream, its grid with Adam state, a point
+// batch, a gradient buffer and a small device status block. One training step
+// (sampler -> binning -> forward -> loss -> backward -> Adam -> gated
+// evaluation -> finalize) is captured once into a CUDA graph whose step
+// counter, error and stop flag live in device memory, so the same graph is
+// replayed for every step. A tick launches one step of every running job on
+// its own stream (their kernels overlap on the GPU), copies each job's status
+// word to pinned host memory behind it and records an event; later ticks read
+// the status only once the event has completed, so the host never blocks on
+// the device inside a tick.
+#include <chrono>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "tg_sdf.cuh"
+
+namespace tg {
+
+struct DevStatus {
+    long long steps;
+    float error;
+    int done;
+};
+
+__global__ void eval_gate_kernel(const int64_t *__restrict__ step, int eval_every, int *__restrict__ gate)
+{
+    *gate = ((*step + 1) % eval_every) == 0 ? 1 : 0;
+}
+
+__global__ void finalize_kernel(int64_t *__restrict__ step, const int *__restrict__ gate, float *__restrict__ err_sum,
+                                float inv_eval, float tol, int max_steps, float *__restrict__ loss,
+                                DevStatus *__restrict__ st)
+{
+    const int64_t s = *step + 1;
+    if (*gate) {
+        const float e = *err_sum * inv_eval;
+        st->error = e;
+        *err_sum = 0.f;
+        if (e < tol) st->done = 1;
+    }
+    *step = s;
+    st->steps = s;
+    if (s >= max_steps) st->done = 1;
+    loss[0] = 0.f;
+    loss[1] = 0.f;
+}
+
+struct Job {
+    tg_job_id id = 0;
+    int kind = 0;                    // 0 fit, 1 query
+    int state = TG_JOB_QUEUED;
+    tg_fit_desc desc{};
+    std::vector<float> sph, box, cdf;
+    size_t bytes = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int64_t steps = 0;
+    float error = -1.f;
+    // fit job device state
+    tg_grid *grid = nullptr;
+    tg_batch *batch = nullptr;
+    float *grad = nullptr;
+    float *shape_dev = nullptr;      // spheres | boxes | cdf
+    float *eval_pts = nullptr;
+    unsigned char *small = nullptr;  // loss[2], err, gate, step, status
+    DevStatus *status_host = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t event = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool in_flight = false;
+    ShapeView sv{};
+    // query
+    tg_job_id grid_of = 0;
+    const float *qpts = nullptr;
+    float *qout = nullptr;
+    int64_t qn = 0;
+
+    float *loss() { return reinterpret_cast<float *>(small); }
+    float *err() { return reinterpret_cast<float *>(small) + 2; }
+    int *gate() { return reinterpret_cast<int *>(small) + 3; }
+    int64_t *step() { return reinterpret_cast<int64_t *>(small + 16); }
+    DevStatus *status() { return reinterpret_cast<DevStatus *>(small + 32); }
+};
+
+static size_t fit_bytes(const tg_fit_desc &d)
+{
+    const int K = num_coefs(3, d.order);
+    const size_t ncoef = (size_t)d.res * d.res * d.res * K;
+    size_t b = ncoef * (4 + 8 + 4) + (d.dtype == TG_F32 ? 0 : ncoef * 2);     // master, Adam m+v, gradient, shadow
+    const size_t nb = (size_t)((d.res - 2) / 8 + 1);
+    const size_t bricks = nb * nb * nb;
+    b += (size_t)d.points_per_step * (16 + 16 + 4 + 4 * 11);                  // records, coarse, perm, staging
+    b += bricks * (3 * 4 + (bricks <= 32768 ? 4 * 152 : 0));                  // offsets and chunk histograms
+    b += (size_t)d.eval_points * 12 + 4096;
+    return b;
+}
+
+static void free_fit_scratch(Job *j)
+{
+    if (j->graph) cudaGraphExecDestroy(j->graph);
+    j->graph = nullptr;
+    if (j->batch) tg_batch_destroy(j->batch);
+    j->batch = nullptr;
+    cudaFree(j->grad); j->grad = nullptr;
+    cudaFree(j->shape_dev); j->shape_dev = nullptr;
+    cudaFree(j->eval_pts); j->eval_pts = nullptr;
+    cudaFree(j->small); j->small = nullptr;
+}
+
+static void free_job(Job *j)
+{
+    if (j->stream) cudaStreamSynchronize(j->stream);
+    free_fit_scratch(j);
+    if (j->grid) tg_destroy(j->grid);
+    j->grid = nullptr;
+    if (j->status_host) cudaFreeHost(j->status_host);
+    j->status_host = nullptr;
+    if (j->event) cudaEventDestroy(j->event);
+    j->event = nullptr;
+    if (j->stream) cudaStreamDestroy(j->stream);
+    j->stream = nullptr;
+}
+
+// Records one training step of a fit job on its stream (captured or direct).
+static tg_status record_step(Job *j)
+{
+    const tg_fit_desc &d = j->desc;
+    tg_status st = sdf_step_impl(j->grid, j->batch, j->sv, nullptr, d.points_per_step, d.seed, 0, j->step(),
+                                 d.lambda_eik, j->grad, j->loss(), j->stream);
+    if (st != TG_OK) return st;
+    tg_adam prm{d.lr, 0.9f, 0.999f, 1e-8f, 1};
+    if ((st = adam_launch(j->grid, j->grad, &prm, j->step(), j->stream)) != TG_OK) return st;
+    eval_gate_kernel<<<1, 1, 0, j->stream>>>(j->step(), d.eval_every, j->gate());
+    if ((st = launch_status("server: eval gate")) != TG_OK) return st;
+    if ((st = sdf_error_impl(j->grid, j->sv, j->eval_pts, d.eval_points, j->err(), j->gate(), j->stream)) != TG_OK)
+        return st;
+    finalize_kernel<<<1, 1, 0, j->stream>>>(j->step(), j->gate(), j->err(), 1.0f / (float)d.eval_points, d.tol,
+                                            d.max_steps, j->loss(), j->status());
+    return launch_status("server: finalize");
+}
+
+static tg_status admit_fit(Job *j)
+{
+    const tg_fit_desc &d = j->desc;
+    tg_status st = cuda_status(cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking), "server: stream");
+    if (st == TG_OK) st = cuda_status(cudaEventCreateWithFlags(&j->event, cudaEventDisableTiming), "server: event");
+    if (st == TG_OK) st = cuda_status(cudaMallocHost(&j->status_host, sizeof(DevStatus)), "server: pinned status");
+    if (st == TG_OK) st = tg_create(3, d.res, d.order, 1, d.dtype, d.seed, d.init_std, &j->grid);
+    if (st == TG_OK) st = tg_batch_create(3, d.res, d.points_per_step, &j->batch);
+    if (st == TG_OK) st = ensure_stage(j->batch, 11 * d.points_per_step, "server: staging");
+    if (st == TG_OK) st = ensure_adam_state(j->grid);
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->grad, (size_t)j->grid->ncoef * 4 + 16), "server: gradient");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->small, 64), "server: status block");
+    const size_t nsh = j->sph.size() + j->box.size() + j->cdf.size();
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->shape_dev, nsh * 4), "server: shape");
+    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->eval_pts, (size_t)d.eval_points * 12), "server: eval points");
+    if (st != TG_OK) return st;
+    cudaStream_t s = j->stream;
+    st = cuda_status(cudaMemsetAsync(j->grad, 0, (size_t)j->grid->ncoef * 4, s), "server: zero gradient");
+    if (st == TG_OK) st = cuda_status(cudaMemsetAsync(j->small, 0, 64, s), "server: zero status");
+    float *sp = j->shape_dev, *bp = sp + j->sph.size(), *cp = bp + j->box.size();
+    if (st == TG_OK && !j->sph.empty())
+        st = cuda_status(cudaMemcpyAsync(sp, j->sph.data(), j->sph.size() * 4, cudaMemcpyHostToDevice, s), "server: shape");
+    if (st == TG_OK && !j->box.empty())
+        st = cuda_status(cudaMemcpyAsync(bp, j->box.data(), j->box.size() * 4, cudaMemcpyHostToDevice, s), "server: shape");
+    if (st == TG_OK)
+        st = cuda_status(cudaMemcpyAsync(cp, j->cdf.data(), j->cdf.size() * 4, cudaMemcpyHostToDevice, s), "server: shape");
+    if (st != TG_OK) return st;
+    tg_shape shape{d.n_spheres, d.n_boxes, sp, bp, cp};
+    if ((st = shape_view(&shape, &j->sv, "server")) != TG_OK) return st;
+    if ((st = tg_sample_sdf_points(&shape, d.seed + 1, 0, d.eval_points, 0.01f, j->eval_pts, s)) != TG_OK) return st;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "server: admission")) != TG_OK) return st;
+    // capture one step as a graph; fall back to direct launches if capture is refused
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const tg_status rec = record_step(j);
+        const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        if (rec == TG_OK && ec == cudaSuccess && graph &&
+            cudaGraphInstantiate(&j->graph, graph, 0) == cudaSuccess) {
+            cudaGraphDestroy(graph);
+        } else {
+            if (graph) cudaGraphDestroy(graph);
+            j->graph = nullptr;
+            cudaGetLastError();
+        }
+    } else {
+        cudaGetLastError();
+    }
+    return TG_OK;
+}
+
+}  // namespace tg
+
+using namespace tg;
+
+struct tg_server {
+    size_t budget = 0, used = 0;
+    int max_running = 1;
+    std::map<tg_job_id, Job *> jobs;
+    std::deque<tg_job_id> queue;
+    tg_job_id next = 1;
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+extern "C" {
+
+tg_status tg_server_create(size_t budget_bytes, int max_running, tg_server **out)
+{
+    if (!out) return fail(TG_EINVAL, "tg_server_create: out is NULL");
+    if (budget_bytes == 0 || max_running < 1) return fail(TG_EINVAL, "tg_server_create: budget > 0, max_running >= 1");
+    tg_server *s = new (std::nothrow) tg_server();
+    if (!s) return fail(TG_ENOMEM, "tg_server_create: host allocation failed");
+    s->budget = budget_bytes;
+    s->max_running = max_running;
+    s->t0 = std::chrono::steady_clock::now();
+    *out = s;
+    return TG_OK;
+}
+
+tg_status tg_server_destroy(tg_server *s)
+{
+    if (!s) return TG_OK;
+    for (auto &kv : s->jobs) {
+        free_job(kv.second);
+        delete kv.second;
+    }
+    delete s;
+    return TG_OK;
+}
+
+double tg_server_time(const tg_server *s) { return s ? s->now() : 0.0; }
+
+tg_status tg_fit_job(tg_server *s, const tg_fit_desc *d, tg_job_id *id)
+{
+    if (!s || !d || !id) return fail(TG_EINVAL, "tg_fit_job: NULL argument");
+    if (d->res < 2 || d->order < 0 || d->order > 2 || d->points_per_step < 1 || d->eval_points < 1 ||
+        d->eval_every < 1 || d->max_steps < 1 || d->n_spheres < 0 || d->n_boxes < 0 ||
+        d->n_spheres + d->n_boxes < 1 || (d->n_spheres && !d->spheres) || (d->n_boxes && !d->boxes) || !d->area_cdf)
+        return fail(TG_EINVAL, "tg_fit_job: bad job description");
+    if (d->dtype != TG_F32 && d->dtype != TG_BF16 && d->dtype != TG_F16) return fail(TG_EINVAL, "tg_fit_job: bad dtype");
+    const size_t need = fit_bytes(*d);
+    if (need > s->budget)
+        return fail(TG_EBUDGET, "tg_fit_job: the job needs %zu bytes, over the budget of %zu", need, s->budget);
+    Job *j = new (std::nothrow) Job();
+    if (!j) return fail(TG_ENOMEM, "tg_fit_job: host allocation failed");
+    j->kind = 0;
+    j->desc = *d;
+    j->sph.assign(d->spheres, d->spheres + 4 * d->n_spheres);
+    j->box.assign(d->boxes, d->boxes + 6 * d->n_boxes);
+    j->cdf.assign(d->area_cdf, d->area_cdf + d->n_spheres + d->n_boxes);
+    j->desc.spheres = j->desc.boxes = j->desc.area_cdf = nullptr;
+    j->bytes = need;
+    std::lock_guard<std::mutex> lock(s->mu);
+    j->id = s->next++;
+    j->t_submit = s->now();
+    s->jobs[j->id] = j;
+    s->queue.push_back(j->id);
+    *id = j->id;
+    return TG_OK;
+}
+
+tg_status tg_query_job(tg_server *s, tg_job_id grid_job, const float *pts, int64_t N, float *out, tg_job_id *id)
+{
+    if (!s || !id || N < 0 || (N > 0 && (!pts || !out))) return fail(TG_EINVAL, "tg_query_job: bad argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(grid_job);
+    if (it == s->jobs.end() || it->second->kind != 0 || it->second->state == TG_JOB_FAILED)
+        return fail(TG_ENOTFOUND, "tg_query_job: no fit job %lld", (long long)grid_job);
+    Job *j = new (std::nothrow) Job();
+    if (!j) return fail(TG_ENOMEM, "tg_query_job: host allocation failed");
+    j->kind = 1;
+    j->grid_of = grid_job;
+    j->qpts = pts; j->qout = out; j->qn = N;
+    j->id = s->next++;
+    j->t_submit = s->now();
+    s->jobs[j->id] = j;
+    s->queue.push_back(j->id);
+    *id = j->id;
+    return TG_OK;
+}
+
+tg_status tg_server_step(tg_server *s, int *pending)
+{
+    if (!s) return fail(TG_EINVAL, "tg_server_step: server is NULL");
+    std::lock_guard<std::mutex> lock(s->mu);
+    int running = 0;
+    // 1. retire finished steps and queries
+    for (auto &kv : s->jobs) {
+        Job *j = kv.second;
+        if (j->state != TG_JOB_RUNNING || !j->in_flight) continue;
+        const cudaError_t q = cudaEventQuery(j->event);
+        if (q == cudaErrorNotReady) continue;
+        j->in_flight = false;
+        if (q != cudaSuccess) {
+            j->state = TG_JOB_FAILED;
+            j->t_done = s->now();
+            cudaGetLastError();
+            continue;
+        }
+        if (j->kind == 1) {
+            j->state = TG_JOB_DONE;
+            j->t_done = s->now();
+            continue;
+        }
+        j->steps = j->status_host->steps;
+        if (j->status_host->error >= 0.f && j->steps >= j->desc.eval_every) j->error = j->status_host->error;
+        if (j->status_host->done) {
+            j->state = TG_JOB_DONE;
+            j->t_done = s->now();
+            free_fit_scratch(j);
+        }
+    }
+    for (auto &kv : s->jobs)
+        if (kv.second->kind == 0 && kv.second->state == TG_JOB_RUNNING) ++running;
+    // 2. admit in arrival order while the budget and the running-job limit allow
+    while (!s->queue.empty()) {
+        Job *j = s->jobs[s->queue.front()];
+        if (j->kind == 1) {
+            auto it = s->jobs.find(j->grid_of);
+            Job *g = it == s->jobs.end() ? nullptr : it->second;
+            if (!g || g->state == TG_JOB_FAILED || !g->grid) {
+                if (g && g->state == TG_JOB_QUEUED) break;          // grid not created yet: keep order
+                j->state = TG_JOB_FAILED;
+                s->queue.pop_front();
+                continue;
+            }
+            j->event = nullptr;
+            tg_status st = cuda_status(cudaEventCreateWithFlags(&j->event, cudaEventDisableTiming), "server: event");
+            if (st == TG_OK) st = tg_query(g->grid, j->qpts, j->qn, j->qout, nullptr, g->stream);
+            if (st == TG_OK) st = cuda_status(cudaEventRecord(j->event, g->stream), "server: query event");
+            j->t_start = s->now();
+            j->state = st == TG_OK ? TG_JOB_RUNNING : TG_JOB_FAILED;
+            j->in_flight = st == TG_OK;
+            s->queue.pop_front();
+            continue;
+        }
+        if (running >= s->max_running || s->used + j->bytes > s->budget) break;
+        s->queue.pop_front();
+        j->t_start = s->now();
+        if (admit_fit(j) != TG_OK) {
+            j->state = TG_JOB_FAILED;
+            j->t_done = s->now();
+            free_job(j);
+            continue;
+        }
+        s->used += j->bytes;
+        j->state = TG_JOB_RUNNING;
+        ++running;
+    }
+    // 3. launch one step of every running fit job whose previous step has retired
+    for (auto &kv : s->jobs) {
+        Job *j = kv.second;
+        if (j->kind != 0 || j->state != TG_JOB_RUNNING || j->in_flight) continue;
+        tg_status st = TG_OK;
+        if (j->graph) st = cuda_status(cudaGraphLaunch(j->graph, j->stream), "server: graph launch");
+        else st = record_step(j);
+        if (st == TG_OK)
+            st = cuda_status(cudaMemcpyAsync(j->status_host, j->status(), sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                                             j->stream), "server: status copy");
+        if (st == TG_OK) st = cuda_status(cudaEventRecord(j->event, j->stream), "server: step event");
+        if (st != TG_OK) {
+            j->state = TG_JOB_FAILED;
+            j->t_done = s->now();
+            continue;
+        }
+        j->in_flight = true;
+    }
+    if (pending) {
+        int p = 0;
+        for (auto &kv : s->jobs) p += (kv.second->state == TG_JOB_QUEUED || kv.second->state == TG_JOB_RUNNING);
+        *pending = p;
+    }
+    return TG_OK;
+}
+
+tg_status tg_poll(tg_server *s, tg_job_id id, tg_job_result *r)
+{
+    if (!s || !r) return fail(TG_EINVAL, "tg_poll: NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end()) return fail(TG_ENOTFOUND, "tg_poll: no job %lld", (long long)id);
+    const Job *j = it->second;
+    r->state = j->state;
+    r->kind = j->kind;
+    r->steps = j->steps;
+    r->error = j->error;
+    r->t_submit = j->t_submit;
+    r->t_start = j->t_start;
+    r->t_done = j->t_done;
+    r->points = j->kind == 0 ? j->steps * j->desc.points_per_step : j->qn;
+    r->bytes = j->bytes;
+    return TG_OK;
+}
+
+tg_status tg_server_grid(tg_server *s, tg_job_id id, tg_grid **grid)
+{
+    if (!s || !grid) return fail(TG_EINVAL, "tg_server_grid: NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end() || it->second->kind != 0 || !it->second->grid)
+        return fail(TG_ENOTFOUND, "tg_server_grid: no resident grid for job %lld", (long long)id);
+    *grid = it->second->grid;
+    return TG_OK;
+}
+
+tg_status tg_release(tg_server *s, tg_job_id id)
+{
+    if (!s) return fail(TG_EINVAL, "tg_release: server is NULL");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end()) return fail(TG_ENOTFOUND, "tg_release: no job %lld", (long long)id);
+    Job *j = it->second;
+    if (j->state == TG_JOB_RUNNING || j->state == TG_JOB_QUEUED) return fail(TG_EBUSY, "tg_release: job is not finished");
+    if (j->kind == 0) {
+        for (auto &kv : s->jobs)   // queries still pending on this grid keep it alive
+            if (kv.second->kind == 1 && kv.second->grid_of == id &&
+                (kv.second->state == TG_JOB_RUNNING || kv.second->state == TG_JOB_QUEUED))
+                return fail(TG_EBUSY, "tg_release: queries on this grid are pending");
+        if (j->grid && j->bytes <= s->used) s->used -= j->bytes;
+    }
+    free_job(j);
+    delete j;
+    s->jobs.erase(it);
+    return TG_OK;
+}
+
+}  // extern "C"

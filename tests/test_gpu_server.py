@@ -1,0 +1,99 @@
+"""The continuous-batching fit / query server: convergence, the same result alone
+and in a mix of concurrent jobs, admission under an HBM budget, queries."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from parity import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def shape_args(shape):
+    return shape.spheres, shape.boxes, shape.area_cdf()
+
+
+def test_single_fit_job_converges(tg):
+    srv = tg.Server(budget_bytes=8 << 30)
+    jid = srv.fit_job(*shape_args(W.sphere_shape()), res=32, order=2, points_per_step=1 << 14,
+                      eval_points=1 << 14, eval_every=10, max_steps=300, tol=3e-3, lr=1e-2)
+    srv.run_until_idle(timeout_s=120)
+    r = srv.poll(jid)
+    assert r["state"] == "done", r
+    assert 0 <= r["error"] < 3e-3 and r["steps"] < 300, r
+    assert r["t_submit"] <= r["t_start"] <= r["t_done"]
+
+
+def run_jobs(tg, specs, budget=16 << 30, max_running=64):
+    srv = tg.Server(budget_bytes=budget, max_running=max_running)
+    ids = [srv.fit_job(*shape_args(sh), **kw) for sh, kw in specs]
+    srv.run_until_idle(timeout_s=120)
+    return srv, ids
+
+
+def test_result_is_the_same_alone_and_in_the_mix(tg):
+    target = (W.union_shape(3), dict(res=48, order=2, seed=11, points_per_step=1 << 14, eval_points=1 << 14,
+                                     eval_every=20, max_steps=120, tol=0.0, lr=5e-3, lambda_eik=0.1))
+    others = [(W.union_shape(10 + k), dict(res=r, order=o, dtype=dt, seed=20 + k, points_per_step=1 << 14,
+                                           eval_points=1 << 13, eval_every=10, max_steps=150, tol=0.0, lr=5e-3))
+              for k, (r, o, dt) in enumerate([(32, 1, "bf16"), (64, 2, "f32"), (40, 2, "f16"), (96, 1, "f32"),
+                                              (32, 2, "f32")])]
+    srv_a, (alone,) = run_jobs(tg, [target])
+    srv_m, ids = run_jobs(tg, others[:3] + [target] + others[3:])
+    mixed = ids[3]
+    ra, rm = srv_a.poll(alone), srv_m.poll(mixed)
+    assert ra["state"] == rm["state"] == "done" and ra["steps"] == rm["steps"] == 120
+    assert abs(ra["error"] - rm["error"]) <= 0.02 * ra["error"], (ra, rm)
+    ca, cm = srv_a.grid_coefs(alone).cpu().numpy(), srv_m.grid_coefs(mixed).cpu().numpy()
+    close = np.abs(ca - cm) <= 1e-3 * np.abs(ca).max()
+    assert close.mean() > 0.99, close.mean()
+    for j in ids:
+        assert srv_m.poll(j)["state"] == "done"
+
+
+def test_admission_waits_for_budget(tg):
+    kw = dict(res=64, order=2, points_per_step=1 << 12, eval_points=1 << 12, eval_every=10, max_steps=40, tol=0.0)
+    srv = tg.Server(budget_bytes=1 << 30, max_running=8)
+    ids = [srv.fit_job(*shape_args(W.sphere_shape()), seed=k, **kw) for k in range(3)]
+    # each job needs about 44 MB: all three fit
+    srv.run_until_idle(timeout_s=120)
+    assert all(srv.poll(j)["state"] == "done" for j in ids)
+    small = tg.Server(budget_bytes=int(1.5 * srv.poll(ids[0])["bytes"]), max_running=8)
+    ids = [small.fit_job(*shape_args(W.sphere_shape()), seed=k, **kw) for k in range(2)]
+    small.step()
+    assert small.poll(ids[0])["state"] == "running" and small.poll(ids[1])["state"] == "queued"
+    for _ in range(100000):                       # a finished job's grid stays charged until released
+        small.step()
+        if small.poll(ids[0])["state"] == "done":
+            break
+    assert small.poll(ids[1])["state"] == "queued"
+    small.release(ids[0])
+    small.run_until_idle(timeout_s=60)
+    r1 = small.poll(ids[1])
+    assert r1["state"] == "done" and r1["t_start"] >= small.time() - 60
+    # the resident grid holds the budget until released
+    with pytest.raises(tg.TGError):
+        tg.Server(budget_bytes=1 << 20).fit_job(*shape_args(W.sphere_shape()), res=128)
+
+
+def test_queries_against_resident_grid(tg):
+    srv = tg.Server(budget_bytes=8 << 30)
+    jid = srv.fit_job(*shape_args(W.sphere_shape()), res=32, order=2, points_per_step=1 << 13, eval_points=1 << 13,
+                      eval_every=10, max_steps=30, tol=0.0, lr=1e-2)
+    pts = to_dev(W.uniform_points(5, 100000))
+    out1 = torch.empty((100000,), device="cuda")
+    q1 = srv.query_job(jid, pts, out1)            # queued behind the job's admission, runs between steps
+    srv.run_until_idle(timeout_s=120)
+    out2 = torch.empty((100000,), device="cuda")
+    q2 = srv.query_job(jid, pts, out2)            # against the finished, resident grid
+    srv.run_until_idle(timeout_s=120)
+    assert srv.poll(q1)["state"] == srv.poll(q2)["state"] == "done"
+    coefs = srv.grid_coefs(jid, which=0)
+    g = tg.tg_create(3, 32, 2, 1, "f32")
+    tg.tg_set_coefs(g, coefs)
+    ref = tg.tg_query(g, pts)[:, 0]
+    torch.testing.assert_close(out2, ref, rtol=0, atol=0)
+    with pytest.raises(tg.TGError):
+        srv.query_job(12345, pts, out2)
+    srv.release(jid)
