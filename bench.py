@@ -295,6 +295,11 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": int(pts_np.nbytes + up_np.nbytes), "d2h_bytes_per_step": int(N * 4)},
         "gpu_launches": launches_per_step * args.steps,
     }
+    if rank == 0 and not args.no_extras:
+        line["configs"] = {"fit_step_256_o2": bench_fit_step(), "query_only_256": bench_query_only(),
+                           "render_160": bench_render()}
+        if args.serving:
+            line["configs"]["serving"] = bench_serving()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, _ = oracle_sample(CPU_SAMPLE)
         line["cpu_baseline"] = {"value": CPU_SAMPLE / dt / 1e6, "unit": "Mpts/s", "cores": threads_used(),
@@ -302,6 +307,170 @@ def run_ours(args, world, rank, local):
                                 "sample": f"{CPU_SAMPLE} of the 2^24 points, same 256^3 order-2 grid, one fwd+bwd"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _time_ms(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def bench_fit_step(steps=10, warmup=3):
+    """SDF fitting step at 256^3 order 2, 2^20 points, L1 + 0.1 eikonal, Adam (FP32 / BF16 / FP16 storage)."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    shape = W.union_shape(0)
+    dsh = tg.DeviceShape(shape.spheres, shape.boxes, shape.area_cdf())
+    n = 1 << 20
+    out = {}
+    for dt in ["f32", "bf16", "f16"]:
+        g = tg.tg_create(3, RES, ORDER, 1, dt, seed=0, init_std=1e-3)
+        batch = tg.tg_batch_create(3, RES, n)
+        grad = torch.zeros(g.n_coefs, device="cuda")
+        loss = torch.zeros(2, device="cuda")
+        k = [0]
+
+        def step():
+            tg.tg_sdf_step(g, batch, dsh, grad, loss, n=n, seed=1, step=k[0], lambda_eik=0.1)
+            tg.tg_adam_step(g, grad, lr=5e-3, step=k[0] + 1)
+            k[0] += 1
+        ms = _time_ms(step, steps, warmup)
+        out[dt] = {"ms_per_step": ms, "Mpts_per_s": n / (ms * 1e-3) / 1e6}
+        del g, batch, grad
+    return {"workload": "SDF fit step, 256^3 order 2, 2^20 points (half uniform, half near-surface), "
+                        "L1 + 0.1 eikonal, Adam; sample+bin+forward+loss+backward+Adam", **out}
+
+
+def bench_query_only(steps=5, warmup=2):
+    """Forward-only query throughput, 2^24 uniform points, 256^3, orders 0/1/2, FP32 vs BF16 storage."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    n = N_POINTS
+    P = torch.rand((n, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    outp = torch.empty((n, 1), device="cuda")
+    batch = tg.tg_batch_create(3, RES, n)
+    res = {}
+    for order in (0, 1, 2):
+        for dt in ("f32", "bf16"):
+            g = tg.tg_create(3, RES, order, 1, dt, seed=0, init_std=1.0)
+
+            def step():
+                tg.tg_batch_bin(batch, P)
+                tg.tg_query_binned(g, batch, out=outp)
+            ms = _time_ms(step, steps, warmup)
+            res[f"order{order}_{dt}"] = round(n / (ms * 1e-3) / 1e6, 1)
+            del g
+    return {"workload": "query forward (bin + binned forward, input order), 256^3, 2^24 uniform points",
+            "unit": "Mpts/s", **res}
+
+
+def bench_render(steps=5, warmup=2):
+    """Ray-march training step: 8192 rays x 256 samples, 160^3 density (order 2) + colour (order 1, 3 ch), BF16."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    res, R, S = 160, 8192, 256
+    dg = tg.tg_create(3, res, 2, 1, "bf16", seed=0, init_std=0.5)
+    cg = tg.tg_create(3, res, 1, 3, "bf16", seed=1, init_std=0.5)
+    o, d = W.random_rays(7, R, radius=1.5, spread=0.35)
+    ro, rd = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    target = torch.rand((R, 3), device="cuda")
+    batch = tg.tg_batch_create(3, res, R * S)
+    dgr = torch.zeros(dg.n_coefs, device="cuda")
+    cgr = torch.zeros(cg.n_coefs, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    k = [0]
+
+    def step():
+        tg.tg_render_rays(dg, cg, ro, rd, S=S, seed=k[0], target=target, batch=batch, density_grad=dgr,
+                          color_grad=cgr, loss_sum=loss)
+        tg.tg_adam_step(dg, dgr, lr=1e-2, step=k[0] + 1)
+        tg.tg_adam_step(cg, cgr, lr=1e-2, step=k[0] + 1)
+        k[0] += 1
+    ms = _time_ms(step, steps, warmup)
+    fwd = _time_ms(lambda: tg.tg_render_rays(dg, cg, ro, rd, S=S, seed=1), steps, warmup)
+    return {"workload": "ray-march training step, 8192 rays x 256 samples, 160^3 BF16 density o2 + colour o1 (3 ch)",
+            "train_ms_per_step": ms, "train_Msamples_per_s": R * S / (ms * 1e-3) / 1e6,
+            "forward_ms": fwd, "forward_Msamples_per_s": R * S / (fwd * 1e-3) / 1e6}
+
+
+def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8):
+    """Poisson arrivals of fit jobs (70 %) and queries (30 %) through the server, against the same trace run
+    one job at a time with FP32 storage."""
+    import math
+
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    t, trace = 0.0, []
+    for k in range(n_jobs):
+        t += rng.exponential(1.0 / rate)
+        if rng.random() < 0.7 or not any(e["kind"] == "fit" for e in trace):
+            trace.append({"kind": "fit", "t": t, "res": int(rng.choice([32, 64, 128, 256])),
+                          "order": int(rng.choice([1, 2])), "dtype": str(rng.choice(["bf16", "f32"])),
+                          "shape": W.union_shape(100 + k), "seed": 100 + k})
+        else:
+            n = int(math.exp(rng.uniform(math.log(1e4), math.log(1e6))))
+            fits = [i for i, e in enumerate(trace) if e["kind"] == "fit"]
+            trace.append({"kind": "query", "t": t, "n": n, "of": int(rng.choice(fits)),
+                          "pts": torch.rand((n, 3), device="cuda")})
+
+    def run(force_fp32, max_running, smallest_first=False):
+        srv = tg.Server(budget_bytes=budget, max_running=max_running, smallest_first=smallest_first)
+        ids, outs = {}, []
+        t0 = srv.time()
+        i = 0
+        while True:
+            now = srv.time() - t0
+            while i < len(trace) and trace[i]["t"] <= now:
+                e = trace[i]
+                if e["kind"] == "fit":
+                    sh = e["shape"]
+                    ids[i] = srv.fit_job(sh.spheres, sh.boxes, sh.area_cdf(), res=e["res"], order=e["order"],
+                                         dtype="f32" if force_fp32 else e["dtype"], seed=e["seed"],
+                                         points_per_step=1 << 16, eval_points=1 << 14, eval_every=10,
+                                         max_steps=1000, tol=2e-3, lr=5e-3, lambda_eik=0.0)
+                else:
+                    out = torch.empty(e["n"], device="cuda")
+                    outs.append(out)
+                    ids[i] = srv.query_job(ids[e["of"]], e["pts"], out)
+                i += 1
+            pending = srv.step()
+            if i == len(trace) and pending == 0:
+                break
+        makespan = srv.time() - t0
+        lat = {"fit": [], "query": []}
+        pts = 0
+        for k, jid in ids.items():
+            r = srv.poll(jid)
+            lat[trace[k]["kind"]].append(r["t_done"] - (t0 + trace[k]["t"]))
+            pts += r["points"]
+        srv.close()
+        pct = lambda a, q: float(np.percentile(a, q)) if a else None
+        return {"fit_p50_s": pct(lat["fit"], 50), "fit_p99_s": pct(lat["fit"], 99),
+                "query_p50_s": pct(lat["query"], 50), "query_p99_s": pct(lat["query"], 99),
+                "makespan_s": makespan, "Mpts_per_s": pts / makespan / 1e6}
+    served = run(False, slots, smallest_first=True)
+    alone = run(True, 1)
+    return {"workload": f"{n_jobs} Poisson arrivals at {rate}/s: 70% SDF fit jobs (res 32/64/128/256, order 1/2, "
+                        "BF16/FP32, 2^16 points/step, L1, until mean |SDF error| < 2e-3 or 1000 steps), 30% queries "
+                        "of 1e4-1e6 points; 64 GB admission budget",
+            "served": {"slots": slots, "admission": "smallest job first", **served},
+            "one_at_a_time_fp32": alone}
 
 
 def profile_once():
@@ -342,6 +511,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the fit / query-only / render lines")
+    ap.add_argument("--serving", action="store_true", help="also run the serving trace (about a minute)")
     ap.add_argument("--profile", action="store_true",
                     help="run each kernel of the step once, untimed (for ncu captures)")
     ap.add_argument("--profile-points", type=int, default=N_POINTS)

@@ -386,6 +386,13 @@ TG_API tg_status tg_server_grid(tg_server *server, tg_job_id id, tg_grid **grid)
 /* Frees a finished fit job's grid (or a finished query's record). TG_EBUSY if it is still running. */
 TG_API tg_status tg_release(tg_server *server, tg_job_id id);
 
+/* Admission order of queued fit jobs: arrival order (default), or the job
+ * with the fewest device bytes first (short jobs overtake long ones; queries
+ * are always admitted first). */
+#define TG_ADMIT_FIFO 0
+#define TG_ADMIT_SMALLEST 1
+TG_API tg_status tg_server_set_policy(tg_server *server, int policy);
+
 /* Seconds on the server's monotonic clock (the clock of tg_job_result). */
 TG_API double tg_server_time(const tg_server *server);
 

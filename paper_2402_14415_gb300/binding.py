@@ -98,6 +98,7 @@ _SIGS = {
     "tg_poll": [_vp, _i64, ctypes.POINTER(JobResult)],
     "tg_server_grid": [_vp, _i64, ctypes.POINTER(_vp)],
     "tg_release": [_vp, _i64],
+    "tg_server_set_policy": [_vp, _int],
     "tg_render_rays": [_vp, _vp, _vp, _vp, _i64, _int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_float, _vp, _vp,
                        _vp, _vp, _vp, _vp, _vp],
 }
@@ -410,11 +411,13 @@ JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 class Server:
     """Continuous-batching fit / query server (tg_server_*)."""
 
-    def __init__(self, budget_bytes: int, max_running: int = 64):
+    def __init__(self, budget_bytes: int, max_running: int = 64, smallest_first: bool = False):
         h = _vp()
         _check(load().tg_server_create(budget_bytes, max_running, ctypes.byref(h)), "tg_server_create")
         self._h = h.value
         self._keep = {}
+        if smallest_first:
+            _check(load().tg_server_set_policy(self._h, 1), "tg_server_set_policy")
 
     def fit_job(self, shape_spheres, shape_boxes, area_cdf, res, order=2, dtype="f32", seed=0, points_per_step=1 << 16,
                 eval_points=1 << 16, eval_every=10, max_steps=1000, tol=2e-3, lr=5e-3, lambda_eik=0.0,

@@ -10,6 +10,7 @@
 // word to pinned host memory behind it and records an event; later ticks read
 // the status only once the event has completed, so the host never blocks on
 // the device inside a tick.
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <map>
@@ -200,6 +201,7 @@ using namespace tg;
 struct tg_server {
     size_t budget = 0, used = 0;
     int max_running = 1;
+    int policy = TG_ADMIT_FIFO;
     std::map<tg_job_id, Job *> jobs;
     std::deque<tg_job_id> queue;
     tg_job_id next = 1;
@@ -235,6 +237,15 @@ tg_status tg_server_destroy(tg_server *s)
 }
 
 double tg_server_time(const tg_server *s) { return s ? s->now() : 0.0; }
+
+tg_status tg_server_set_policy(tg_server *s, int policy)
+{
+    if (!s || (policy != TG_ADMIT_FIFO && policy != TG_ADMIT_SMALLEST))
+        return fail(TG_EINVAL, "tg_server_set_policy: bad argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->policy = policy;
+    return TG_OK;
+}
 
 tg_status tg_fit_job(tg_server *s, const tg_fit_desc *d, tg_job_id *id)
 {
@@ -318,7 +329,16 @@ tg_status tg_server_step(tg_server *s, int *pending)
     }
     for (auto &kv : s->jobs)
         if (kv.second->kind == 0 && kv.second->state == TG_JOB_RUNNING) ++running;
-    // 2. admit in arrival order while the budget and the running-job limit allow
+    // 2. admit while the budget and the running-job limit allow: arrival order,
+    //    or (TG_ADMIT_SMALLEST) the queued fit job with the fewest bytes first;
+    //    queries always go first, in arrival order
+    if (s->policy == TG_ADMIT_SMALLEST && s->queue.size() > 1) {
+        std::stable_sort(s->queue.begin(), s->queue.end(), [&](tg_job_id a, tg_job_id b) {
+            const Job *ja = s->jobs[a], *jb = s->jobs[b];
+            const size_t ka = ja->kind == 1 ? 0 : ja->bytes, kb = jb->kind == 1 ? 0 : jb->bytes;
+            return ka < kb;
+        });
+    }
     while (!s->queue.empty()) {
         Job *j = s->jobs[s->queue.front()];
         if (j->kind == 1) {
