@@ -406,7 +406,7 @@ def bench_render(steps=5, warmup=2):
             "forward_ms": fwd, "forward_Msamples_per_s": R * S / (fwd * 1e-3) / 1e6}
 
 
-def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8):
+def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8, deadline_s=120.0):
     """Poisson arrivals of fit jobs (70 %) and queries (30 %) through the server, against the same trace run
     one job at a time with FP32 storage."""
     import math
@@ -452,6 +452,9 @@ def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8):
             pending = srv.step()
             if i == len(trace) and pending == 0:
                 break
+            if srv.time() - t0 > deadline_s:
+                srv.close()
+                raise RuntimeError(f"serving trace did not drain within {deadline_s} s")
         makespan = srv.time() - t0
         lat = {"fit": [], "query": []}
         pts = 0

@@ -329,9 +329,11 @@ tg_status tg_server_step(tg_server *s, int *pending)
     }
     for (auto &kv : s->jobs)
         if (kv.second->kind == 0 && kv.second->state == TG_JOB_RUNNING) ++running;
-    // 2. admit while the budget and the running-job limit allow: arrival order,
-    //    or (TG_ADMIT_SMALLEST) the queued fit job with the fewest bytes first;
-    //    queries always go first, in arrival order
+    // 2. admission scan over the queue: arrival order, or (TG_ADMIT_SMALLEST)
+    //    fit jobs by increasing device bytes. A query runs as soon as its grid
+    //    exists and otherwise stays queued without blocking anything; the first
+    //    fit job that does not fit the budget or the running-job limit stops
+    //    admission of every fit job behind it (no overtaking by larger jobs).
     if (s->policy == TG_ADMIT_SMALLEST && s->queue.size() > 1) {
         std::stable_sort(s->queue.begin(), s->queue.end(), [&](tg_job_id a, tg_job_id b) {
             const Job *ja = s->jobs[a], *jb = s->jobs[b];
@@ -339,15 +341,20 @@ tg_status tg_server_step(tg_server *s, int *pending)
             return ka < kb;
         });
     }
-    while (!s->queue.empty()) {
-        Job *j = s->jobs[s->queue.front()];
+    std::deque<tg_job_id> keep;
+    bool fit_blocked = false;
+    for (tg_job_id id : s->queue) {
+        Job *j = s->jobs[id];
         if (j->kind == 1) {
             auto it = s->jobs.find(j->grid_of);
             Job *g = it == s->jobs.end() ? nullptr : it->second;
+            if (g && g->state == TG_JOB_QUEUED) {         // grid not created yet
+                keep.push_back(id);
+                continue;
+            }
             if (!g || g->state == TG_JOB_FAILED || !g->grid) {
-                if (g && g->state == TG_JOB_QUEUED) break;          // grid not created yet: keep order
                 j->state = TG_JOB_FAILED;
-                s->queue.pop_front();
+                j->t_done = s->now();
                 continue;
             }
             j->event = nullptr;
@@ -357,11 +364,14 @@ tg_status tg_server_step(tg_server *s, int *pending)
             j->t_start = s->now();
             j->state = st == TG_OK ? TG_JOB_RUNNING : TG_JOB_FAILED;
             j->in_flight = st == TG_OK;
-            s->queue.pop_front();
+            if (st != TG_OK) j->t_done = j->t_start;
             continue;
         }
-        if (running >= s->max_running || s->used + j->bytes > s->budget) break;
-        s->queue.pop_front();
+        if (fit_blocked || running >= s->max_running || s->used + j->bytes > s->budget) {
+            fit_blocked = true;
+            keep.push_back(id);
+            continue;
+        }
         j->t_start = s->now();
         if (admit_fit(j) != TG_OK) {
             j->state = TG_JOB_FAILED;
@@ -373,6 +383,7 @@ tg_status tg_server_step(tg_server *s, int *pending)
         j->state = TG_JOB_RUNNING;
         ++running;
     }
+    s->queue.swap(keep);
     // 3. launch one step of every running fit job whose previous step has retired
     for (auto &kv : s->jobs) {
         Job *j = kv.second;

@@ -97,3 +97,21 @@ def test_queries_against_resident_grid(tg):
     with pytest.raises(tg.TGError):
         srv.query_job(12345, pts, out2)
     srv.release(jid)
+
+
+def test_smallest_first_admission(tg):
+    """Fit jobs are admitted by increasing bytes; a query whose grid is still queued waits without blocking."""
+    srv = tg.Server(budget_bytes=16 << 30, max_running=1, smallest_first=True)
+    kw = dict(order=2, points_per_step=1 << 12, eval_points=1 << 12, eval_every=10, max_steps=20, tol=0.0)
+    big = srv.fit_job(*shape_args(W.sphere_shape()), res=96, **kw)
+    mid = srv.fit_job(*shape_args(W.sphere_shape()), res=64, **kw)
+    pts = to_dev(W.uniform_points(7, 5000))
+    out = torch.empty((5000,), device="cuda")
+    q = srv.query_job(mid, pts, out)              # sorted ahead of its own (queued) fit job
+    small = srv.fit_job(*shape_args(W.sphere_shape()), res=32, **kw)
+    srv.run_until_idle(timeout_s=120)
+    r = {j: srv.poll(j) for j in (big, mid, small, q)}
+    assert all(x["state"] == "done" for x in r.values()), r
+    # one slot, all four queued before the first tick: small, then mid (and its query once its grid exists), then big
+    assert r[small]["t_start"] <= r[small]["t_done"] <= r[mid]["t_start"] <= r[q]["t_start"]
+    assert r[mid]["t_done"] <= r[big]["t_start"]
