@@ -194,7 +194,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tg.load()
-    launches_per_step = 6      # 4 binning kernels + forward + backward
+    launches_per_step = 9      # 5 binning kernels, forward, scatter, gather, backward
 
     g = tg.tg_create(3, RES, ORDER, C, "f32", seed=0, init_std=1.0)
     N = N_POINTS
@@ -203,14 +203,22 @@ def run_ours(args, world, rank, local):
     P = torch.from_numpy(pts_np).to(dev)
     U = torch.from_numpy(up_np).to(dev)
     out = torch.empty((N, 1), device=dev)
+    out_b = torch.empty((N, 1), device=dev)      # f in binned order
+    up_b = torch.empty((N, 1), device=dev)       # dL/df in binned order
     grad = torch.zeros(g.n_coefs, device=dev)
     batch = tg.tg_batch_create(3, RES, N)
     stream = torch.cuda.current_stream()
 
+    # one step = bin, forward, f back to input order, dL/df to binned order, backward
+    calls = [("bin", lambda pts, up: tg.tg_batch_bin(batch, pts)),
+             ("forward", lambda pts, up: tg.tg_query_binned(g, batch, out=out_b, binned_order=True)),
+             ("scatter", lambda pts, up: tg.tg_batch_scatter(batch, out_b, dst=out)),
+             ("gather", lambda pts, up: tg.tg_batch_gather(batch, up, dst=up_b)),
+             ("backward", lambda pts, up: tg.tg_query_backward_binned(g, batch, up_b, grad, binned_order=True))]
+
     def step(pts=P, upstream=U):
-        tg.tg_batch_bin(batch, pts)
-        tg.tg_query_binned(g, batch, out=out)
-        tg.tg_query_backward_binned(g, batch, upstream, grad)
+        for _, call in calls:
+            call(pts, upstream)
 
     for _ in range(args.warmup):
         step()
@@ -218,30 +226,22 @@ def run_ours(args, world, rank, local):
 
     # device-timed region
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(args.steps)]
     with Clocks(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
         ev[0].record(stream)
         for s in range(args.steps):
-            e_bin, e_fwd, e_bwd, e_end = kev[s]
-            e_bin.record(stream)
-            tg.tg_batch_bin(batch, P)
-            e_fwd.record(stream)
-            tg.tg_query_binned(g, batch, out=out)
-            e_bwd.record(stream)
-            tg.tg_query_backward_binned(g, batch, U, grad)
-            e_end.record(stream)
+            for k, (_, call) in enumerate(calls):
+                kev[s][k].record(stream)
+                call(P, U)
+            kev[s][-1].record(stream)
         ev[1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
     clocks = clk.summary()
     ms = max_over_ranks(world, ev[0].elapsed_time(ev[1])) / args.steps
-    t_bin = statistics.mean(a.elapsed_time(b) for a, b, _, _ in kev)
-    t_fwd = statistics.mean(b.elapsed_time(c) for _, b, c, _ in kev)
-    t_bwd = statistics.mean(c.elapsed_time(d) for _, _, c, d in kev)
+    kernels = {name: statistics.mean(e[k].elapsed_time(e[k + 1]) for e in kev) for k, (name, _) in enumerate(calls)}
     value = world * N / (ms * 1e-3) / 1e6
 
     # end to end through the public API: pinned host inputs in, f back to the host
@@ -272,9 +272,8 @@ def run_ours(args, world, rank, local):
 
     hbm, peak_kind = peaks()
     fwd_bytes, bwd_bytes = algorithmic_bytes(N, RES ** 3)
-    kernels = {"bin": t_bin, "forward": t_fwd, "backward": t_bwd}
     dom = max(kernels, key=kernels.get)
-    dom_bytes = {"bin": None, "forward": fwd_bytes, "backward": bwd_bytes}[dom]
+    dom_bytes = {"forward": fwd_bytes, "backward": bwd_bytes}.get(dom)
     achieved = (dom_bytes / (kernels[dom] * 1e-3) / 1e9) if dom_bytes else None
     line = {
         "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world, "steps": args.steps,
@@ -284,7 +283,7 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (points 201 MB, grid 671 MB, gradient 671 MB)",
                    "parallelism": f"replicas x{world}"},
         "kernel_ms": {k: round(v, 4) for k, v in kernels.items()},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
                      "traffic": TRAFFIC.get(dom),
                      "model": "compulsory bytes: 16 B/point + K*4 B (fwd) or 2*K*4 B (bwd) per touched vertex"},
@@ -492,9 +491,15 @@ def profile_once():
     gx = torch.empty((n, 1, 3), device="cuda")
     grad = torch.zeros(g.n_coefs, device="cuda")
     batch = tg.tg_batch_create(3, RES, n)
+    out_b = torch.empty_like(out)
+    up_b = torch.empty_like(U)
+    # the bench step's launches, in its order: bin, forward, scatter, gather, backward
     tg.tg_batch_bin(batch, P)
-    tg.tg_query_binned(g, batch, out=out)
-    tg.tg_query_backward_binned(g, batch, U, grad)
+    tg.tg_query_binned(g, batch, out=out_b, binned_order=True)
+    tg.tg_batch_scatter(batch, out_b, dst=out)
+    tg.tg_batch_gather(batch, U, dst=up_b)
+    tg.tg_query_backward_binned(g, batch, up_b, grad, binned_order=True)
+    # spatial-gradient variants of the two brick kernels (input order)
     tg.tg_query_binned(g, batch, out=out, grad_x=gx)
     tg.tg_query_backward_binned(g, batch, U, grad, dL_dgradx=UG)
     tg.tg_adam_step(g, grad, lr=1e-3, step=1)
@@ -502,9 +507,14 @@ def profile_once():
     print("profile pass done, timeouts:", tg.tg_batch_timeouts(batch))
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
-# ncu capture summarised in profiles/; None when the kernel changed since.
-TRAFFIC = {"forward": None, "backward": None, "bin": None}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# full-size launch captured by `ncu --set full ... python bench.py --profile`
+# (profiles/query_step_256_o2_2e24_full.md); None once the kernel has changed since.
+TRAFFIC = {"forward": 0.939984e9 + 64.454912e6, "backward": 1.006787e9 + 615.565568e6,
+           "bin": None, "scatter": 0.198197e9 + 119.575296e6, "gather": 0.297337e9 + 62.650368e6}
+KERNEL_NAMES = {"bin": "bin_* (5 kernels, tg_batch_bin)", "forward": "brick_fwd_kernel (tg_query_binned)",
+                "scatter": "permute_rows_kernel (tg_batch_scatter)", "gather": "permute_rows_kernel (tg_batch_gather)",
+                "backward": "brick_bwd_kernel (tg_query_backward_binned)"}
 
 
 def main():

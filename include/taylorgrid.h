@@ -197,6 +197,19 @@ TG_API tg_status tg_batch_order(const tg_batch *batch, int32_t *idx, tg_stream s
 /* The binned points in binned order (device, N x 3 FP32). */
 TG_API tg_status tg_batch_points(const tg_batch *batch, float *pts, tg_stream stream);
 
+/* Move per-point rows of `width` floats (1..64) between the two orders of
+ * the points last binned. tg_batch_gather: dst (device, N x width, binned
+ * order) [p] = src (device, N x width, input order) [idx[p]].
+ * tg_batch_scatter: dst (input order) [idx[p]] = src (binned order) [p].
+ * idx is the order of tg_batch_order. Together with TG_ORDER_BINNED these
+ * give the same results as TG_ORDER_INPUT, one launch per call; they let a
+ * caller permute several arrays at once or keep them in binned order.
+ * src and dst must not overlap. N = 0 is a no-op.
+ * Errors: TG_EINVAL (NULL batch or array, width out of range, src == dst),
+ * TG_EDEVICE. */
+TG_API tg_status tg_batch_gather(const tg_batch *batch, const float *src, int width, float *dst, tg_stream stream);
+TG_API tg_status tg_batch_scatter(const tg_batch *batch, const float *src, int width, float *dst, tg_stream stream);
+
 /* The binned kernels wait on their TMA copies with a 2 s limit; a wait that
  * gives up sets a device flag instead of hanging. Synchronously reads that
  * flag into *timed_out (non-zero = some launch since the last call gave up,

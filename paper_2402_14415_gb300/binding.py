@@ -83,6 +83,8 @@ _SIGS = {
     "tg_batch_order": [_vp, _vp, _vp],
     "tg_batch_points": [_vp, _vp, _vp],
     "tg_batch_timeouts": [_vp, ctypes.POINTER(_int)],
+    "tg_batch_gather": [_vp, _vp, _int, _vp, _vp],
+    "tg_batch_scatter": [_vp, _vp, _int, _vp, _vp],
     "tg_query_noalloc": [_vp, _vp, _i64, _vp, _vp, _vp],
     "tg_adam_step": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
     "tg_sdf_eval_target": [ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
@@ -310,6 +312,28 @@ def tg_batch_points(batch: Batch, stream=None) -> torch.Tensor:
     _check(load().tg_batch_points(batch.handle, _ptr(pts, "pts") if batch.n else None, _stream(stream)),
            "tg_batch_points")
     return pts
+
+
+def _permute_rows(fn: str, batch: Batch, src: torch.Tensor, dst, stream):
+    N = batch.n
+    width = src.numel() // N if N else (src.shape[1] if src.dim() > 1 else 1)
+    if N and src.numel() != N * width:
+        raise ValueError(f"{fn}: src has {src.numel()} elements, not a multiple of N = {N}")
+    if dst is None:
+        dst = torch.empty_like(src)
+    _check(getattr(load(), fn)(batch.handle, _ptr(src, "src", numel=N * width) if N else None, width,
+                               _ptr(dst, "dst", numel=N * width) if N else None, _stream(stream)), fn)
+    return dst
+
+
+def tg_batch_gather(batch: Batch, src: torch.Tensor, dst=None, stream=None) -> torch.Tensor:
+    """Rows of an input-order per-point array in binned order: dst[p] = src[idx[p]]."""
+    return _permute_rows("tg_batch_gather", batch, src, dst, stream)
+
+
+def tg_batch_scatter(batch: Batch, src: torch.Tensor, dst=None, stream=None) -> torch.Tensor:
+    """Rows of a binned-order per-point array back in input order: dst[idx[p]] = src[p]."""
+    return _permute_rows("tg_batch_scatter", batch, src, dst, stream)
 
 
 def tg_batch_timeouts(batch: Batch) -> int:

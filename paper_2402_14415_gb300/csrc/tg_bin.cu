@@ -309,6 +309,27 @@ gather_upstream_kernel(const int *__restrict__ perm, const float *__restrict__ d
     }
 }
 
+// Per-point rows of `width` floats between the two orders. GATHER: binned
+// from input, dst[p] = src[perm[p]]; otherwise SCATTER: dst[perm[p]] = src[p].
+// WIDTH > 0 fixes the row width at compile time (1 and 3 are the common ones).
+template <bool GATHER, int WIDTH>
+__global__ void __launch_bounds__(256)
+permute_rows_kernel(const int *__restrict__ perm, const float *__restrict__ src, int64_t N, int width,
+                    float *__restrict__ dst)
+{
+    const int w = WIDTH > 0 ? WIDTH : width;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = __ldg(perm + p);
+        const int64_t from = (GATHER ? n : p) * w, to = (GATHER ? p : n) * w;
+        if (WIDTH > 0) {
+#pragma unroll
+            for (int j = 0; j < WIDTH; ++j) dst[to + j] = __ldg(src + from + j);
+        } else {
+            for (int j = 0; j < w; ++j) dst[to + j] = __ldg(src + from + j);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
 batch_points_kernel(const float4 *__restrict__ sorted, int64_t N, float *__restrict__ pts)
 {
@@ -425,6 +446,28 @@ tg_status gather_upstream(const tg_batch *bt, int C, const float *dL_df, const f
     gather_upstream_kernel<<<grid_for((const void *)gather_upstream_kernel, 256, bt->n), 256, 0, s>>>(
         bt->perm, dL_df, dL_dgradx, bt->n, C, bt->stage);
     return launch_status("tg_query_backward_binned: gather upstream");
+}
+
+template <bool GATHER>
+static tg_status permute_rows(const tg_batch *b, const float *src, int width, float *dst, cudaStream_t s,
+                              const char *what)
+{
+    if (!b) return fail(TG_EINVAL, "%s: batch is NULL", what);
+    if (width < 1 || width > 64) return fail(TG_EINVAL, "%s: width %d outside 1..64", what, width);
+    if (b->n == 0) return TG_OK;
+    if (!src || !dst) return fail(TG_EINVAL, "%s: NULL array", what);
+    if (src == dst) return fail(TG_EINVAL, "%s: src and dst must not alias", what);
+    if (width == 1) {
+        auto k = permute_rows_kernel<GATHER, 1>;
+        k<<<grid_for((const void *)k, 256, b->n), 256, 0, s>>>(b->perm, src, b->n, 1, dst);
+    } else if (width == 3) {
+        auto k = permute_rows_kernel<GATHER, 3>;
+        k<<<grid_for((const void *)k, 256, b->n), 256, 0, s>>>(b->perm, src, b->n, 3, dst);
+    } else {
+        auto k = permute_rows_kernel<GATHER, 0>;
+        k<<<grid_for((const void *)k, 256, b->n), 256, 0, s>>>(b->perm, src, b->n, width, dst);
+    }
+    return launch_status(what);
 }
 
 }  // namespace tg
@@ -548,6 +591,16 @@ tg_status tg_batch_points(const tg_batch *b, float *pts, tg_stream stream)
     batch_points_kernel<<<grid_for((const void *)batch_points_kernel, 256, b->n), 256, 0, (cudaStream_t)stream>>>(
         b->sorted, b->n, pts);
     return launch_status("tg_batch_points");
+}
+
+tg_status tg_batch_gather(const tg_batch *b, const float *src, int width, float *dst, tg_stream stream)
+{
+    return permute_rows<true>(b, src, width, dst, (cudaStream_t)stream, "tg_batch_gather");
+}
+
+tg_status tg_batch_scatter(const tg_batch *b, const float *src, int width, float *dst, tg_stream stream)
+{
+    return permute_rows<false>(b, src, width, dst, (cudaStream_t)stream, "tg_batch_scatter");
 }
 
 tg_status tg_batch_timeouts(tg_batch *b, int *timed_out)

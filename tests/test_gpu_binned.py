@@ -79,6 +79,29 @@ def test_binned_order_io(tg, C, order):
     torch.testing.assert_close(g_b, g_i, rtol=1e-4, atol=1e-4)
 
 
+@pytest.mark.parametrize("width", [1, 3, 10])
+def test_batch_gather_scatter(tg, width):
+    """tg_batch_gather / tg_batch_scatter are the permutation of tg_batch_order, row by row, bit for bit."""
+    res = 26
+    pts = np.concatenate([points(3, res, 20001, seed=4), clustered(777)])
+    N = pts.shape[0]
+    batch = tg.tg_batch_create(3, res, N)
+    tg.tg_batch_bin(batch, to_dev(pts))
+    idx = tg.tg_batch_order(batch).long()
+    src = torch.randn((N, width), device="cuda")
+    binned = tg.tg_batch_gather(batch, src)
+    assert torch.equal(binned, src[idx])
+    back = tg.tg_batch_scatter(batch, binned)
+    assert torch.equal(back, src)
+    # the public permutation + TG_ORDER_BINNED reproduce TG_ORDER_INPUT
+    g = tg.tg_create(3, res, 2, 1, "f32", seed=1, init_std=0.5)
+    out_i = tg.tg_query_binned(g, batch)
+    out_b = tg.tg_query_binned(g, batch, binned_order=True)
+    assert torch.equal(tg.tg_batch_scatter(batch, out_b), out_i)
+    with pytest.raises(tg.TGError):
+        tg.tg_batch_gather(batch, src, dst=src)
+
+
 def test_binned_value_only_backward_and_rebin(tg):
     res, order, C = 26, 2, 1
     g = tg.tg_create(3, res, order, C, "f32", seed=3, init_std=0.3)

@@ -60,6 +60,10 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     lib.tg_query.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                              ctypes.c_void_p]
     assert lib.tg_query(None, None, 0, None, None, None) == 1
+    for fn in ("tg_batch_gather", "tg_batch_scatter"):
+        f = getattr(lib, fn)
+        f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        assert f(None, None, 1, None, None) == 1
 
 
 def test_product_path_has_no_oracle_reference():
