@@ -194,7 +194,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tg.load()
-    launches_per_step = 9      # 5 binning kernels, forward, scatter, gather, backward
+    launches_per_step = 7      # 5 binning kernels, forward, backward
 
     g = tg.tg_create(3, RES, ORDER, C, "f32", seed=0, init_std=1.0)
     N = N_POINTS
@@ -203,18 +203,14 @@ def run_ours(args, world, rank, local):
     P = torch.from_numpy(pts_np).to(dev)
     U = torch.from_numpy(up_np).to(dev)
     out = torch.empty((N, 1), device=dev)
-    out_b = torch.empty((N, 1), device=dev)      # f in binned order
-    up_b = torch.empty((N, 1), device=dev)       # dL/df in binned order
     grad = torch.zeros(g.n_coefs, device=dev)
     batch = tg.tg_batch_create(3, RES, N)
     stream = torch.cuda.current_stream()
 
-    # one step = bin, forward, f back to input order, dL/df to binned order, backward
+    # one step = bin, forward (f in input order), backward (dL/df in input order)
     calls = [("bin", lambda pts, up: tg.tg_batch_bin(batch, pts)),
-             ("forward", lambda pts, up: tg.tg_query_binned(g, batch, out=out_b, binned_order=True)),
-             ("scatter", lambda pts, up: tg.tg_batch_scatter(batch, out_b, dst=out)),
-             ("gather", lambda pts, up: tg.tg_batch_gather(batch, up, dst=up_b)),
-             ("backward", lambda pts, up: tg.tg_query_backward_binned(g, batch, up_b, grad, binned_order=True))]
+             ("forward", lambda pts, up: tg.tg_query_binned(g, batch, out=out)),
+             ("backward", lambda pts, up: tg.tg_query_backward_binned(g, batch, up, grad))]
 
     def step(pts=P, upstream=U):
         for _, call in calls:
@@ -491,15 +487,11 @@ def profile_once():
     gx = torch.empty((n, 1, 3), device="cuda")
     grad = torch.zeros(g.n_coefs, device="cuda")
     batch = tg.tg_batch_create(3, RES, n)
-    out_b = torch.empty_like(out)
-    up_b = torch.empty_like(U)
-    # the bench step's launches, in its order: bin, forward, scatter, gather, backward
+    # the bench step's launches, in its order: bin, forward, backward
     tg.tg_batch_bin(batch, P)
-    tg.tg_query_binned(g, batch, out=out_b, binned_order=True)
-    tg.tg_batch_scatter(batch, out_b, dst=out)
-    tg.tg_batch_gather(batch, U, dst=up_b)
-    tg.tg_query_backward_binned(g, batch, up_b, grad, binned_order=True)
-    # spatial-gradient variants of the two brick kernels (input order)
+    tg.tg_query_binned(g, batch, out=out)
+    tg.tg_query_backward_binned(g, batch, U, grad)
+    # spatial-gradient variants of the two brick kernels
     tg.tg_query_binned(g, batch, out=out, grad_x=gx)
     tg.tg_query_backward_binned(g, batch, U, grad, dL_dgradx=UG)
     tg.tg_adam_step(g, grad, lr=1e-3, step=1)
@@ -510,10 +502,8 @@ def profile_once():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # full-size launch captured by `ncu --set full ... python bench.py --profile`
 # (profiles/query_step_256_o2_2e24_full.md); None once the kernel has changed since.
-TRAFFIC = {"forward": 0.939984e9 + 64.454912e6, "backward": 1.006787e9 + 615.565568e6,
-           "bin": None, "scatter": 0.198197e9 + 119.575296e6, "gather": 0.297337e9 + 62.650368e6}
+TRAFFIC = {"forward": None, "backward": None, "bin": None}
 KERNEL_NAMES = {"bin": "bin_* (5 kernels, tg_batch_bin)", "forward": "brick_fwd_kernel (tg_query_binned)",
-                "scatter": "permute_rows_kernel (tg_batch_scatter)", "gather": "permute_rows_kernel (tg_batch_gather)",
                 "backward": "brick_bwd_kernel (tg_query_backward_binned)"}
 
 

@@ -162,7 +162,8 @@ typedef struct tg_batch tg_batch;   /* opaque; owns the scratch of one binned ba
 
 /* Create a batch able to hold up to max_points points for grids of the
  * given dim and res (the brick count depends on res). Allocates device
- * scratch (about 24 bytes per point plus 8 bytes per brick). */
+ * scratch (about 36 bytes per point plus 12 bytes per brick, and 4 bytes per
+ * brick for each of the per-SM binning histograms). */
 TG_API tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out);
 TG_API tg_status tg_batch_destroy(tg_batch *batch);
 
@@ -176,14 +177,13 @@ TG_API tg_status tg_batch_bin(tg_batch *batch, const float *pts, int64_t N, tg_s
 
 /* Same outputs as tg_query / tg_query_backward for the points last binned.
  * With TG_ORDER_INPUT the per-point arrays (out, grad_x, dL_df, dL_dgradx)
- * are in the caller's original order: the kernels work in binned order on a
- * staging buffer and one extra pass scatters the outputs back (or gathers the
- * upstream gradients). With TG_ORDER_BINNED they are in binned order and the
- * extra pass is skipped - use it when the per-point work around the query
- * (a loss, a sampler) can run in that order too. The staging buffer holds
- * 4 floats per point from tg_batch_create; spatial gradients with more than
- * one channel need more and the first such call grows it (synchronously).
- * Errors: TG_EINVAL (shape or order flag), TG_ENOMEM, TG_EDEVICE. */
+ * are in the caller's original order: each binned record carries its input
+ * index, and the kernels write the outputs (or read the upstream gradients)
+ * at that index. With TG_ORDER_BINNED they are in binned order (slot p of
+ * tg_batch_order), which keeps those accesses within each brick's range -
+ * use it when the per-point work around the query (a loss, a sampler) can
+ * run in that order too. Neither order needs scratch beyond the batch.
+ * Errors: TG_EINVAL (shape or order flag), TG_EDEVICE. */
 TG_API tg_status tg_query_binned(const tg_grid *grid, const tg_batch *batch,
                                  float *out, float *grad_x, int order_flags, tg_stream stream);
 TG_API tg_status tg_query_backward_binned(const tg_grid *grid, const tg_batch *batch,
@@ -223,11 +223,10 @@ TG_API tg_status tg_batch_timeouts(tg_batch *batch, int *timed_out);
  * them this call bins the N points (device, N x 3) and evaluates f (and, if
  * grad_x is not NULL, the world-unit spatial gradient) exactly like
  * tg_batch_bin + tg_query_binned, with all scratch held in one fixed array
- * of about 9.4 MB compiled into the library (every GPU that loads the
+ * of about 5.6 MB compiled into the library (every GPU that loads the
  * library keeps it until the process exits).
- * Limits: N <= 262144 points and res <= 257 (at most 32768 bricks), and
- * grad_x only for one-channel grids; other requests fail with TG_EINVAL and a
- * message. 3-D grids only, with the same shape rules as tg_query_binned.
+ * Limits: N <= 262144 points and res <= 257 (at most 32768 bricks); other
+ * requests fail with TG_EINVAL and a message. 3-D grids only, with the same shape rules as tg_query_binned.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.
  * Every call reuses the same array and leaves its contents behind (the call

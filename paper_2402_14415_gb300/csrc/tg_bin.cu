@@ -5,9 +5,10 @@
 // the histograms into per-chunk write cursors, and two place passes (coarse
 // runs, then a fine scatter inside an L2-resident region) write every point
 // into brick order using shared-memory atomics only. Larger grids fall back
-// to global-atomic counting. The binning also records the permutation, so
-// the brick kernels read and write in binned order and the original order is
-// restored (or gathered) by one separate pass over an L2-sized array.
+// to global-atomic counting. Every binned record keeps its input index (in
+// its fourth word), so the brick kernels can address per-point arrays in
+// either order; the binning also writes the permutation itself (slot ->
+// input index) for tg_batch_order and the row permutations.
 #include <stdlib.h>
 
 #include <mutex>
@@ -279,36 +280,6 @@ bin_scatter_kernel(const float *__restrict__ pts, int64_t N, int res, int nbx, i
     }
 }
 
-// Original-order outputs from binned-order staging: out[perm[p]] = stage[p].
-__global__ void __launch_bounds__(256)
-unpermute_kernel(const int *__restrict__ perm, const float *__restrict__ stage, int64_t N, int C,
-                 float *__restrict__ out, float *__restrict__ gx)
-{
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = __ldg(perm + p);
-        for (int ch = 0; ch < C; ++ch) out[n * C + ch] = __ldg(stage + p * C + ch);
-        if (gx) {
-            const float *g = stage + N * C + p * 3 * C;
-            for (int j = 0; j < 3 * C; ++j) gx[n * 3 * C + j] = __ldg(g + j);
-        }
-    }
-}
-
-// Binned-order upstream gradients: stage[p] = dLdf[perm[p]] (then dLdg).
-__global__ void __launch_bounds__(256)
-gather_upstream_kernel(const int *__restrict__ perm, const float *__restrict__ dLdf, const float *__restrict__ dLdg,
-                       int64_t N, int C, float *__restrict__ stage)
-{
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = __ldg(perm + p);
-        for (int ch = 0; ch < C; ++ch) stage[p * C + ch] = __ldg(dLdf + n * C + ch);
-        if (dLdg) {
-            float *g = stage + N * C + p * 3 * C;
-            for (int j = 0; j < 3 * C; ++j) g[j] = __ldg(dLdg + n * 3 * C + j);
-        }
-    }
-}
-
 // Per-point rows of `width` floats between the two orders. GATHER: binned
 // from input, dst[p] = src[perm[p]]; otherwise SCATTER: dst[perm[p]] = src[p].
 // WIDTH > 0 fixes the row width at compile time (1 and 3 are the common ones).
@@ -359,11 +330,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 tg_status make_brick_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem, int res, int nv,
-                         int box_z)
+                         int box_inner, int box_z)
 {
     auto fn = encode_fn();
     if (!fn) return fail(TG_EDEVICE, "cuTensorMapEncodeTiled is unavailable from the driver");
-    const int bxi = box_inner_host(nv, elem);
+    const int bxi = box_inner;
+    if (bxi < kBV * nv || (bxi * elem) % 16 != 0) return fail(TG_EINVAL, "binned path: bad box row of %d elements", bxi);
     if (bxi > 256) return fail(TG_EINVAL, "binned path: a brick row of %d elements exceeds the TMA box limit", bxi);
     if (((size_t)res * nv * elem) % 16 != 0)
         return fail(TG_EINVAL, "binned path: res * K * channels * elem (%d * %d * %d) must be a multiple of 16 bytes",
@@ -434,20 +406,6 @@ tg_status ensure_aux(tg_batch *bt, int64_t floats, const char *who)
     return TG_OK;
 }
 
-tg_status unpermute_outputs(const tg_batch *bt, int C, float *out, float *grad_x, cudaStream_t s)
-{
-    unpermute_kernel<<<grid_for((const void *)unpermute_kernel, 256, bt->n), 256, 0, s>>>(bt->perm, bt->stage, bt->n,
-                                                                                          C, out, grad_x);
-    return launch_status("tg_query_binned: unpermute");
-}
-
-tg_status gather_upstream(const tg_batch *bt, int C, const float *dL_df, const float *dL_dgradx, cudaStream_t s)
-{
-    gather_upstream_kernel<<<grid_for((const void *)gather_upstream_kernel, 256, bt->n), 256, 0, s>>>(
-        bt->perm, dL_df, dL_dgradx, bt->n, C, bt->stage);
-    return launch_status("tg_query_backward_binned: gather upstream");
-}
-
 template <bool GATHER>
 static tg_status permute_rows(const tg_batch *b, const float *src, int width, float *dst, cudaStream_t s,
                               const char *what)
@@ -502,11 +460,7 @@ tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
     if (st == TG_OK && b->G)
         st = cuda_status(cudaMalloc(&b->coarse, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->perm, (max_points > 0 ? max_points : 1) * sizeof(int)), "tg_batch_create");
-    if (st == TG_OK) {
-        b->stage_floats = 4 * (max_points > 0 ? max_points : 1);
-        b->stage_owned = true;
-        st = cuda_status(cudaMalloc(&b->stage, (size_t)b->stage_floats * sizeof(float)), "tg_batch_create");
-    }
+    b->stage_owned = true;        // staging for the fused training steps is allocated on first use
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->status, sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->offsets, 0, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->status, 0, sizeof(int)), "tg_batch_create");

@@ -20,7 +20,7 @@ struct tg_batch {
     float4 *sorted;       // max_points: (x, y, z, original index as int bits)
     float4 *coarse;       // max_points: the same records grouped by coarse bin (histogram binning)
     int *perm;            // max_points: original index of every binned slot
-    float *stage;         // binned-order staging of outputs / upstream gradients
+    float *stage;         // binned-order per-point staging of the fused training steps (grown on demand)
     int64_t stage_floats; // capacity of stage
     bool stage_owned;     // stage was allocated by the batch (false: caller-provided scratch)
     float *aux;           // per-sample workspace of the renderer (grown on demand)
@@ -52,8 +52,11 @@ __device__ __forceinline__ int brick_of(const int *c, int nbx, int nby)
 
 // Tensor map of a res^3 x nv array (coefficients or gradient) viewed as the
 // 3-D tensor [z][y][x * nv], with a box of box_z planes of 9 brick rows.
+// 3-D tensor map of a res^3 grid of nv-element vertex blocks viewed as
+// [z][y][x * nv], with a box of `box_inner` elements x 9 rows x box_z planes
+// (box_inner >= 9 nv, a multiple of 16 bytes, at most 256).
 tg_status make_brick_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem, int res, int nv,
-                         int box_z);
+                         int box_inner, int box_z);
 
 // Opts a kernel in to more than 48 KB of dynamic shared memory.
 tg_status set_smem(const void *kernel, int bytes);
@@ -64,10 +67,5 @@ tg_status check_pair(const tg_grid *g, const tg_batch *bt, const char *who);
 // synchronously; a caller-provided buffer that is too small is an error).
 tg_status ensure_stage(tg_batch *bt, int64_t floats, const char *who);
 tg_status ensure_aux(tg_batch *bt, int64_t floats, const char *who);
-
-// out[perm[p]] = stage[p] (and the spatial-gradient block that follows it).
-tg_status unpermute_outputs(const tg_batch *bt, int C, float *out, float *grad_x, cudaStream_t s);
-// stage[p] = dL_df[perm[p]] (and dL_dgradx after it).
-tg_status gather_upstream(const tg_batch *bt, int C, const float *dL_df, const float *dL_dgradx, cudaStream_t s);
 
 }  // namespace tg

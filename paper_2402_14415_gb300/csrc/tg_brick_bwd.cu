@@ -1,11 +1,14 @@
 // Brick-binned coefficient gradient: the adjoint of Eq. 2 - Eq. 4.
 //
 // One block per 8^3-cell brick. The brick's points are staged in shared
-// memory with their upstream gradients and counting-sorted by cell; the
+// memory with their upstream gradients (read at the binned slot, or at the
+// input index every binned record carries) and counting-sorted by cell; the
 // vertex-centric gather (tg_gather.cuh) then sums every vertex's
 // contributions in registers, without atomics, into a shared 9^3 tile, and
 // one TMA bulk-tensor reduce-add (element-wise atomic at L2) adds the tile to
 // the global gradient, which also combines the faces neighbouring bricks share.
+// A brick whose points fit one round stores the tile instead of zeroing it
+// and adding to it.
 #include "tg_gather.cuh"
 
 namespace tg {
@@ -23,7 +26,7 @@ struct BwdLayout {
     static constexpr int bytes = (tile_floats + rec_floats + GatherInts::total) * 4;
 };
 
-template <int ORDER, int C, bool HAS_G>
+template <int ORDER, int C, bool HAS_G, bool IN_ORDER>
 __global__ void __launch_bounds__(kBwdThreads)
 brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int nby,
                  const float4 *__restrict__ sorted, const int *__restrict__ offsets, const float *__restrict__ dLdf,
@@ -48,8 +51,14 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
     const float scale = (float)(res - 1);
     const int tid = threadIdx.x;
 
-    for (int j = tid; j < L::tile_floats / 4; j += kBwdThreads)
-        reinterpret_cast<float4 *>(tile)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool single = p1 - p0 <= kPChunk;
+    if (single) {   // the round stores every vertex block; only the row padding needs zeros
+        constexpr int PAD = BXI - kBV * NV;
+        for (int j = tid; j < kBV * kBV * PAD; j += kBwdThreads) tile[(j / PAD) * BXI + kBV * NV + j % PAD] = 0.f;
+    } else {
+        for (int j = tid; j < L::tile_floats / 4; j += kBwdThreads)
+            reinterpret_cast<float4 *>(tile)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     for (int base = p0; base < p1; base += kPChunk) {
         const int cnt = min(kPChunk, p1 - base);
@@ -57,7 +66,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
         __syncthreads();
         int my_lc[kPPT];
         float my_t[kPPT][3];
-        int my_n[kPPT];                              // binned slot of the point (upstream index)
+        int my_n[kPPT];                              // upstream index: input index or binned slot
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int i = tid + r * kBwdThreads;
@@ -67,7 +76,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
                 const float x[3] = {q.x, q.y, q.z};
                 int c[3];
                 locate<3>(x, res, scale, c, my_t[r]);
-                my_n[r] = base + i;
+                my_n[r] = IN_ORDER ? __float_as_int(q.w) : base + i;
                 my_lc[r] = (c[0] - x0) + kBrick * ((c[1] - y0) + kBrick * (c[2] - z0));
                 atomicAdd(cell_cur + my_lc[r], 1);
             }
@@ -94,7 +103,8 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
                 *reinterpret_cast<float4 *>(rec + pos * RS + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
         __syncthreads();
-        gather_round<ORDER, C, HAS_G, kBwdThreads, BXI>(rec, ints, tile, scale);
+        if (single) gather_round<ORDER, C, HAS_G, kBwdThreads, BXI, true>(rec, ints, tile, scale);
+        else gather_round<ORDER, C, HAS_G, kBwdThreads, BXI, false>(rec, ints, tile, scale);
         __syncthreads();
     }
 
@@ -107,31 +117,35 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
     }
 }
 
+template <int ORDER, int C, bool HAS_G, bool IN_ORDER>
+static tg_status launch_bwd(const CUtensorMap &map, const tg_grid *g, const tg_batch *bt, const float *uf,
+                            const float *ug, cudaStream_t s)
+{
+    auto k = brick_bwd_kernel<ORDER, C, HAS_G, IN_ORDER>;
+    const int smem = BwdLayout<ORDER, C, HAS_G>::bytes;
+    tg_status st = set_smem((const void *)k, smem);
+    if (st != TG_OK) return st;
+    k<<<(unsigned)bt->nbricks, kBwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted, bt->offsets,
+                                                       uf, ug);
+    return launch_status("tg_query_backward_binned");
+}
+
 template <int DIM, int ORDER, int C>
 static tg_status binned_bwd(const tg_grid *g, const tg_batch *bt, const float *uf, const float *ug, float *grad,
-                            cudaStream_t s)
+                            bool in_order, cudaStream_t s)
 {
     if constexpr (DIM != 3) {
         return fail(TG_EINVAL, "binned path is 3-D only");
     } else {
         constexpr int NV = Basis<3, ORDER>::K * C;
         CUtensorMap map;
-        tg_status st = make_brick_map(&map, grad, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->res, NV, kBV);
+        tg_status st = make_brick_map(&map, grad, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->res, NV,
+                                      BoxInner<float, NV>::value, kBV);
         if (st != TG_OK) return st;
-        if (ug) {
-            auto k = brick_bwd_kernel<ORDER, C, true>;
-            const int smem = BwdLayout<ORDER, C, true>::bytes;
-            if ((st = set_smem((const void *)k, smem)) != TG_OK) return st;
-            k<<<(unsigned)bt->nbricks, kBwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
-                                                               bt->offsets, uf, ug);
-        } else {
-            auto k = brick_bwd_kernel<ORDER, C, false>;
-            const int smem = BwdLayout<ORDER, C, false>::bytes;
-            if ((st = set_smem((const void *)k, smem)) != TG_OK) return st;
-            k<<<(unsigned)bt->nbricks, kBwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
-                                                               bt->offsets, uf, nullptr);
-        }
-        return launch_status("tg_query_backward_binned");
+        if (ug) return in_order ? launch_bwd<ORDER, C, true, true>(map, g, bt, uf, ug, s)
+                                : launch_bwd<ORDER, C, true, false>(map, g, bt, uf, ug, s);
+        return in_order ? launch_bwd<ORDER, C, false, true>(map, g, bt, uf, nullptr, s)
+                        : launch_bwd<ORDER, C, false, false>(map, g, bt, uf, nullptr, s);
     }
 }
 
@@ -150,15 +164,8 @@ extern "C" tg_status tg_query_backward_binned(const tg_grid *g, const tg_batch *
     if (bt->n == 0) return TG_OK;
     if (!dL_df || !coef_grad) return fail(TG_EINVAL, "tg_query_backward_binned: NULL dL_df or coef_grad");
     cudaStream_t s = (cudaStream_t)stream;
-    const float *uf = dL_df, *ug = dL_dgradx;
-    if (flags == TG_ORDER_INPUT) {
-        const int64_t need = bt->n * g->C * (dL_dgradx ? 4 : 1);
-        if ((st = ensure_stage(bt, need, "tg_query_backward_binned")) != TG_OK) return st;
-        if ((st = gather_upstream(bt, g->C, dL_df, dL_dgradx, s)) != TG_OK) return st;
-        uf = bt->stage;
-        ug = dL_dgradx ? bt->stage + bt->n * g->C : nullptr;
-    }
-#define TG_BB(D, O, C) binned_bwd<D, O, C>(g, bt, uf, ug, coef_grad, s)
+    const bool in_order = flags == TG_ORDER_INPUT;
+#define TG_BB(D, O, C) binned_bwd<D, O, C>(g, bt, dL_df, dL_dgradx, coef_grad, in_order, s)
     return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_BB);
 #undef TG_BB
 }

@@ -1,9 +1,12 @@
 // Brick-binned forward query (Eq. 2 - Eq. 4): one block per 8^3-cell brick
 // TMA-loads the brick's 9^3 vertex blocks into shared memory with one 3-D
-// tiled copy, then evaluates its points from there using per-point delta
-// tables (one FMA per coefficient and corner). Outputs are written in binned
-// order (coalesced); original order is restored by one separate pass.
-#include "tg_binned.cuh"
+// tiled copy and, while the copy is in flight, counting-sorts the brick's
+// points by cell in shared memory, so that the lanes of a warp evaluate
+// neighbouring cells and their corner reads from the tile fall into distinct
+// banks. Each point is evaluated with per-point delta tables (one FMA per
+// coefficient and corner). Outputs go straight to the caller's order: the
+// binned slot, or the input index that every binned record carries.
+#include "tg_gather.cuh"
 
 namespace tg {
 
@@ -42,7 +45,20 @@ __device__ __forceinline__ void load_block_smem(const T *p, float *out)
     }
 }
 
-template <typename T, int ORDER, int C, bool WANT_GRAD>
+constexpr int kFwdChunk = 1024;                       // points sorted per round
+constexpr int kFwdPPT = kFwdChunk / kFwdThreads;
+
+template <typename T, int NV>
+struct FwdLayout {
+    static constexpr int row = BoxInner<T, NV>::value;                 // tile row pitch (elements)
+    static constexpr int tile_bytes = BoxInner<T, NV>::tile_bytes;
+    static constexpr int bar_off = (tile_bytes + 15) / 16 * 16;
+    static constexpr int ints_off = bar_off + 16;                    // cell counters + scan workspace
+    static constexpr int rec_off = (ints_off + SortInts::total * 4 + 15) / 16 * 16;
+    static constexpr int bytes = rec_off + kFwdChunk * 16;
+};
+
+template <typename T, int ORDER, int C, bool WANT_GRAD, bool IN_ORDER>
 __global__ void __launch_bounds__(kFwdThreads)
 brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int nby,
                  const float4 *__restrict__ sorted, const int *__restrict__ offsets, float *__restrict__ out,
@@ -50,10 +66,14 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
 {
     constexpr int K = Basis<3, ORDER>::K;
     constexpr int NV = K * C;
-    constexpr int BXI = BoxInner<T, NV>::value;
+    using L = FwdLayout<T, NV>;
+    constexpr int BXI = L::row;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);
-    uint64_t &bar = *reinterpret_cast<uint64_t *>(smem_raw + BoxInner<T, NV>::tile_bytes);
+    uint64_t &bar = *reinterpret_cast<uint64_t *>(smem_raw + L::bar_off);
+    int *ints = reinterpret_cast<int *>(smem_raw + L::ints_off);
+    int *cell_cur = ints + SortInts::cell_cur;
+    float4 *recs = reinterpret_cast<float4 *>(smem_raw + L::rec_off);
 
     const int b = blockIdx.x;
     const int p0 = offsets[b], p1 = offsets[b + 1];
@@ -66,69 +86,117 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, BoxInner<T, NV>::tile_bytes);
+        mbar_arrive_expect_tx(&bar, L::tile_bytes);
         tma_load_3d(tile, &cmap, x0 * NV, y0, z0, &bar);
-    }
-    if (!mbar_wait_bounded(&bar, 0)) {
-        if (threadIdx.x == 0) atomicExch(status, 1);
-        mbar_wait_bounded(&bar, 0);          // second bounded wait for the copy in flight
-        return;
     }
 
     const float scale = (float)(res - 1), h = 1.0f / (float)(res - 1);
-    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const float4 q = sorted[p];
-        const int64_t n = p;                       // binned-order output slot
-        const float x[3] = {q.x, q.y, q.z};
-        int c[3];
-        float t[3];
-        locate<3>(x, res, scale, c, t);
-        const PointTables3<ORDER> P(t, h);
-        const T *cell = tile + ((c[2] - z0) * kBV + (c[1] - y0)) * BXI + (c[0] - x0) * NV;
-        float f[C], gu[C][3];
+    bool waited = false;
+    for (int base = p0; base < p1; base += kFwdChunk) {
+        const int cnt = min(kFwdChunk, p1 - base);
+        // counting sort of this round's points by cell (x fastest)
+        for (int j = threadIdx.x; j < kBrickCells; j += kFwdThreads) cell_cur[j] = 0;
+        __syncthreads();
+        float4 q[kFwdPPT];
+        int lc[kFwdPPT];
 #pragma unroll
-        for (int ch = 0; ch < C; ++ch) {
-            f[ch] = 0.f;
-            gu[ch][0] = gu[ch][1] = gu[ch][2] = 0.f;
-        }
-        for_corners<0>([&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            constexpr int off = ((I >> 2) & 1) * kBV * BXI + ((I >> 1) & 1) * BXI + (I & 1) * NV;
-            float th[NV];
-            load_block_smem<T, NV>(cell + off, th);
-            const float w = P.template weight<I>();
-            float dw[3];
-            if constexpr (WANT_GRAD) {
-                P.template dweight<I>(dw);
-                dw[0] *= scale; dw[1] *= scale; dw[2] *= scale;     // d w / d x
+        for (int r = 0; r < kFwdPPT; ++r) {
+            const int i = threadIdx.x + r * kFwdThreads;
+            lc[r] = -1;
+            if (i < cnt) {
+                q[r] = sorted[base + i];
+                const float x[3] = {q[r].x, q[r].y, q[r].z};
+                int c[3];
+                float t[3];
+                locate<3>(x, res, scale, c, t);
+                lc[r] = (c[0] - x0) + kBrick * ((c[1] - y0) + kBrick * (c[2] - z0));
+                if (!IN_ORDER) q[r].w = __int_as_float(base + i);      // output slot: the binned slot
+                atomicAdd(cell_cur + lc[r], 1);
             }
+        }
+        __syncthreads();
+        gather_scan_cells<kFwdThreads, SortInts>(ints);
+#pragma unroll
+        for (int r = 0; r < kFwdPPT; ++r)
+            if (lc[r] >= 0) recs[atomicAdd(cell_cur + lc[r], 1)] = q[r];
+        __syncthreads();
+        if (!waited) {
+            waited = true;
+            if (!mbar_wait_bounded(&bar, 0)) {
+                if (threadIdx.x == 0) atomicExch(status, 1);
+                mbar_wait_bounded(&bar, 0);          // second bounded wait for the copy in flight
+                return;
+            }
+        }
+        for (int j = threadIdx.x; j < cnt; j += kFwdThreads) {
+            const float4 qq = recs[j];
+            const int64_t n = __float_as_int(qq.w);
+            const float x[3] = {qq.x, qq.y, qq.z};
+            int c[3];
+            float t[3];
+            locate<3>(x, res, scale, c, t);
+            const PointTables3<ORDER> P(t, h);
+            const T *cell = tile + ((c[2] - z0) * kBV + (c[1] - y0)) * BXI + (c[0] - x0) * NV;
+            float f[C], gu[C][3];
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
-                const float Tv = P.template value<I>(th + ch * K);       // Eq. 3
-                f[ch] = fmaf(w, Tv, f[ch]);                               // Eq. 4
+                f[ch] = 0.f;
+                gu[ch][0] = gu[ch][1] = gu[ch][2] = 0.f;
+            }
+            for_corners<0>([&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                constexpr int off = ((I >> 2) & 1) * kBV * BXI + ((I >> 1) & 1) * BXI + (I & 1) * NV;
+                float th[NV];
+                load_block_smem<T, NV>(cell + off, th);
+                const float w = P.template weight<I>();
+                float dw[3];
                 if constexpr (WANT_GRAD) {
-                    float g[3];
-                    P.template gradient<I>(th + ch * K, g);
+                    P.template dweight<I>(dw);
+                    dw[0] *= scale; dw[1] *= scale; dw[2] *= scale;     // d w / d x
+                }
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) gu[ch][d] = fmaf(dw[d], Tv, fmaf(w, g[d], gu[ch][d]));
+                for (int ch = 0; ch < C; ++ch) {
+                    const float Tv = P.template value<I>(th + ch * K);       // Eq. 3
+                    f[ch] = fmaf(w, Tv, f[ch]);                               // Eq. 4
+                    if constexpr (WANT_GRAD) {
+                        float g[3];
+                        P.template gradient<I>(th + ch * K, g);
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) gu[ch][d] = fmaf(dw[d], Tv, fmaf(w, g[d], gu[ch][d]));
+                    }
+                }
+            });
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) {
+                out[n * C + ch] = f[ch];
+                if constexpr (WANT_GRAD) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) gx[(n * C + ch) * 3 + d] = gu[ch][d];
                 }
             }
-        });
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) {
-            out[n * C + ch] = f[ch];
-            if constexpr (WANT_GRAD) {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) gx[(n * C + ch) * 3 + d] = gu[ch][d];
-            }
         }
+        __syncthreads();                             // recs and counters are reused by the next round
     }
 }
 
 template <typename T>
 struct BinnedFwd {
+    template <bool WANT_GRAD, bool IN_ORDER, int ORDER, int C>
+    static tg_status launch(const CUtensorMap &map, const tg_grid *g, const tg_batch *bt, float *out, float *gx,
+                            cudaStream_t s)
+    {
+        constexpr int NV = Basis<3, ORDER>::K * C;
+        auto k = brick_fwd_kernel<T, ORDER, C, WANT_GRAD, IN_ORDER>;
+        const int smem = FwdLayout<T, NV>::bytes;
+        tg_status st = set_smem((const void *)k, smem);
+        if (st != TG_OK) return st;
+        k<<<(unsigned)bt->nbricks, kFwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted, bt->offsets,
+                                                           out, gx, bt->status);
+        return launch_status("tg_query_binned");
+    }
+
     template <int DIM, int ORDER, int C>
-    static tg_status run(const tg_grid *g, const tg_batch *bt, float *out, float *gx, cudaStream_t s)
+    static tg_status run(const tg_grid *g, const tg_batch *bt, float *out, float *gx, bool in_order, cudaStream_t s)
     {
         if constexpr (DIM != 3) {
             return fail(TG_EINVAL, "binned path is 3-D only");
@@ -138,21 +206,12 @@ struct BinnedFwd {
             const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                            : (g->dtype == TG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-            tg_status st = make_brick_map(&map, g->store, dt, (int)sizeof(T), g->res, NV, kBV);
+            tg_status st = make_brick_map(&map, g->store, dt, (int)sizeof(T), g->res, NV, FwdLayout<T, NV>::row, kBV);
             if (st != TG_OK) return st;
-            const int smem = BoxInner<T, NV>::tile_bytes + 16;     // tile + mbarrier
-            if (gx) {
-                auto k = brick_fwd_kernel<T, ORDER, C, true>;
-                if ((st = set_smem((const void *)k, smem)) != TG_OK) return st;
-                k<<<(unsigned)bt->nbricks, kFwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
-                                                                   bt->offsets, out, gx, bt->status);
-            } else {
-                auto k = brick_fwd_kernel<T, ORDER, C, false>;
-                if ((st = set_smem((const void *)k, smem)) != TG_OK) return st;
-                k<<<(unsigned)bt->nbricks, kFwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
-                                                                   bt->offsets, out, nullptr, bt->status);
-            }
-            return launch_status("tg_query_binned");
+            if (gx) return in_order ? launch<true, true, ORDER, C>(map, g, bt, out, gx, s)
+                                    : launch<true, false, ORDER, C>(map, g, bt, out, gx, s);
+            return in_order ? launch<false, true, ORDER, C>(map, g, bt, out, nullptr, s)
+                            : launch<false, false, ORDER, C>(map, g, bt, out, nullptr, s);
         }
     }
 };
@@ -171,19 +230,12 @@ extern "C" tg_status tg_query_binned(const tg_grid *g, const tg_batch *bt_in, fl
     if (bt->n == 0) return TG_OK;
     if (!out) return fail(TG_EINVAL, "tg_query_binned: out is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    float *o = out, *gx = grad_x;
-    if (flags == TG_ORDER_INPUT) {
-        const int64_t need = bt->n * g->C * (grad_x ? 4 : 1);
-        if ((st = ensure_stage(bt, need, "tg_query_binned")) != TG_OK) return st;
-        o = bt->stage;
-        gx = grad_x ? bt->stage + bt->n * g->C : nullptr;
-    }
-#define TG_QB(D, O, C)                                                                  \
-    (g->dtype == TG_F32    ? BinnedFwd<float>::run<D, O, C>(g, bt, o, gx, s)            \
-     : g->dtype == TG_BF16 ? BinnedFwd<__nv_bfloat16>::run<D, O, C>(g, bt, o, gx, s)    \
-                           : BinnedFwd<__half>::run<D, O, C>(g, bt, o, gx, s))
+    const bool in_order = flags == TG_ORDER_INPUT;
+#define TG_QB(D, O, C)                                                                            \
+    (g->dtype == TG_F32    ? BinnedFwd<float>::run<D, O, C>(g, bt, out, grad_x, in_order, s)            \
+     : g->dtype == TG_BF16 ? BinnedFwd<__nv_bfloat16>::run<D, O, C>(g, bt, out, grad_x, in_order, s)    \
+                           : BinnedFwd<__half>::run<D, O, C>(g, bt, out, grad_x, in_order, s))
     st = TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_QB);
 #undef TG_QB
-    if (st != TG_OK || flags == TG_ORDER_BINNED) return st;
-    return unpermute_outputs(bt, g->C, out, grad_x, s);
+    return st;
 }

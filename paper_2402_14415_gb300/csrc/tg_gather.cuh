@@ -1,5 +1,6 @@
 // Vertex-centric coefficient-gradient gather over one brick (the adjoint of
-// Eq. 2 - Eq. 4), shared by the binned backward and the fused training steps.
+// Eq. 2 - Eq. 4) for the binned backward, and the block scans and cell sort
+// that the binned forward shares with it.
 //
 // The brick's staged points are sorted by cell in shared memory. Every
 // thread owns whole vertices: for a vertex it walks the points of its (up to)
@@ -62,19 +63,27 @@ __device__ __forceinline__ int gather_block_scan(int v, int *warp_tmp, int &tota
     return before + incl - v;
 }
 
+// Integer workspace of a cell sort alone (the forward's).
+struct SortInts {
+    static constexpr int cell_cur = 0;                          // kBrickCells
+    static constexpr int cell_off = cell_cur + kBrickCells;     // kBrickCells + 1
+    static constexpr int warp_tmp = cell_off + kBrickCells + 1 + 3;   // 32
+    static constexpr int total = warp_tmp + 32;
+};
+
 // Scan of the 512 cell counts in ints[cell_cur] into ints[cell_off] and back
 // into ints[cell_cur] (as placement cursors). All NT threads take part.
-template <int NT>
+template <int NT, typename LAY = GatherInts>
 __device__ __forceinline__ void gather_scan_cells(int *ints)
 {
     static_assert(kBrickCells % NT == 0, "");
     constexpr int CPT = kBrickCells / NT;
-    int *cur = ints + GatherInts::cell_cur, *off = ints + GatherInts::cell_off;
+    int *cur = ints + LAY::cell_cur, *off = ints + LAY::cell_off;
     int v[CPT], sum = 0;
 #pragma unroll
     for (int k = 0; k < CPT; ++k) { v[k] = cur[CPT * threadIdx.x + k]; sum += v[k]; }
     int total;
-    int run = gather_block_scan<NT>(sum, ints + GatherInts::warp_tmp, total);
+    int run = gather_block_scan<NT>(sum, ints + LAY::warp_tmp, total);
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
         off[CPT * threadIdx.x + k] = run;
@@ -201,11 +210,14 @@ __device__ __forceinline__ void gather_vertex(int v, const float *rec, const int
 }
 
 // One gather round: all NT threads take the vertices in load order and add
-// their sums into the shared tile (row stride BXI floats, vertex stride NV).
-template <int ORDER, int C, bool HAS_G, int NT, int BXI>
+// their sums into the shared tile (row stride BXI floats, vertex stride NV),
+// or, with ASSIGN (the brick's only round), store them over whatever the tile
+// held - every vertex of the tile is written, empty ones with zeros.
+template <int ORDER, int C, bool HAS_G, int NT, int BXI, bool ASSIGN>
 __device__ __forceinline__ void gather_round(const float *rec, int *ints, float *tile, float scale)
 {
     constexpr int NV = Basis<3, ORDER>::K * C;
+    constexpr bool PAIRS = NV % 2 == 0 && BXI % 2 == 0;     // vertex blocks are 8-byte aligned
     gather_order_vertices<NT>(ints);
     const int *order = ints + GatherInts::vorder, *off = ints + GatherInts::cell_off;
     for (int j = threadIdx.x; j < kBrickVerts; j += NT) {
@@ -215,8 +227,22 @@ __device__ __forceinline__ void gather_round(const float *rec, int *ints, float 
         for (int k = 0; k < NV; ++k) acc[k] = 0.f;
         gather_vertex<ORDER, C, HAS_G>(v, rec, off, scale, acc);
         float *d = tile + (v / kBV) * BXI + (v % kBV) * NV;
+        if constexpr (PAIRS) {
+            float2 *d2 = reinterpret_cast<float2 *>(d);
 #pragma unroll
-        for (int k = 0; k < NV; ++k) d[k] += acc[k];
+            for (int k = 0; k < NV / 2; ++k) {
+                float2 o = make_float2(acc[2 * k], acc[2 * k + 1]);
+                if (!ASSIGN) {
+                    const float2 e = d2[k];
+                    o.x += e.x;
+                    o.y += e.y;
+                }
+                d2[k] = o;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) d[k] = ASSIGN ? acc[k] : d[k] + acc[k];
+        }
     }
 }
 

@@ -1,8 +1,8 @@
 // tg_query_noalloc: the brick-binned forward query for callers that cannot
 // allocate device memory. All of its scratch (brick counters, offsets, write
-// cursors, the sorted point records, the permutation, the output staging and
-// a status word) lives in one file-scope device array of fixed size; the call
-// itself never allocates.
+// cursors, the sorted point records, the permutation and a status word) lives
+// in one file-scope device array of fixed size; the call itself never
+// allocates.
 #include <mutex>
 
 #include "tg_binned.cuh"
@@ -19,10 +19,9 @@ struct NoallocScratch {
     int status[4];
     float4 sorted[kNoallocMaxPoints];
     int perm[kNoallocMaxPoints];
-    float stage[4 * kNoallocMaxPoints];
 };
 
-// About 9.4 MB; every GPU that loads the library holds it until the process exits.
+// About 5.6 MB; every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
 
 // Device address of the scratch array, looked up once per device with that
@@ -83,9 +82,9 @@ extern "C" tg_status tg_query_noalloc(const tg_grid *g, const float *pts, int64_
     b.hist = nullptr;
     b.sorted = s->sorted;
     b.perm = s->perm;
-    b.stage = s->stage;
-    b.stage_floats = 4 * kNoallocMaxPoints;
-    b.stage_owned = false;      // a request needing more staging fails instead of allocating
+    b.stage = nullptr;             // the input-order forward writes straight to out / grad_x
+    b.stage_floats = 0;
+    b.stage_owned = false;
     b.status = s->status;
     cudaGetDevice(&b.device);
     st = cuda_status(cudaMemsetAsync(s->status, 0, sizeof(int), (cudaStream_t)stream), "tg_query_noalloc: clear status");

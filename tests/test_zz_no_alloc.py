@@ -39,3 +39,14 @@ def test_noalloc_rejects_sizes_over_its_limit(tg):
     big = tg.tg_create(3, 300, 0, 1, "f32")
     with pytest.raises(tg.TGError, match="bricks"):
         tg.tg_query_noalloc(big, torch.rand((16, 3), device="cuda"))
+
+
+def test_noalloc_spatial_gradient_with_several_channels(tg):
+    res = 20
+    g = tg.tg_create(3, res, 1, 3, "f32", seed=6, init_std=0.5)
+    P = to_dev(W.uniform_points(13, 50000))
+    out, gx = tg.tg_query_noalloc(g, P, want_grad=True)
+    ref, ref_gx = tg.tg_query(g, P, want_grad=True)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(out, ref, rtol=VAL_RTOL, atol=1e-6)
+    torch.testing.assert_close(gx, ref_gx, rtol=VAL_RTOL, atol=1e-5)
