@@ -134,9 +134,15 @@ def max_over_ranks(world, value: float) -> float:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seeds(rank: int):
+    """Seeds of one replica's inputs: (points, upstream). Every rank draws its own points."""
+    return 1 + rank, 4 + rank
 
 
 # ---------------------------------------------------------------------------
@@ -198,8 +204,9 @@ def run_ours(args, world, rank, local):
 
     g = tg.tg_create(3, RES, ORDER, C, "f32", seed=0, init_std=1.0)
     N = N_POINTS
-    pts_np = W.uniform_points(1 + rank, N)
-    up_np = W.normal(4 + rank, W.STREAM_UPSTREAM, np.arange(N, dtype=np.uint64)).astype(np.float32).reshape(-1, 1)
+    seed_pts, seed_up = replica_seeds(rank)
+    pts_np = W.uniform_points(seed_pts, N)
+    up_np = W.normal(seed_up, W.STREAM_UPSTREAM, np.arange(N, dtype=np.uint64)).astype(np.float32).reshape(-1, 1)
     P = torch.from_numpy(pts_np).to(dev)
     U = torch.from_numpy(up_np).to(dev)
     out = torch.empty((N, 1), device=dev)

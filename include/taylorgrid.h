@@ -140,10 +140,13 @@ TG_API tg_status tg_query(const tg_grid *grid, const float *pts, int64_t N,
  * linear in the coefficients, f = A theta, so this computes A^T). Given the
  * upstream gradients dL_df (device, N x channels) and optionally dL_dgradx
  * (device, N x channels x dim, world units; NULL = none), ADDS
- *   dL/dtheta_{v,c,k} += sum_n w_i(t_n) phi_k(delta_i) dL_df[n,c]
- *                        + (res-1) sum_d dL_dgradx[n,c,d] d/du_d(w_i phi_k)
- * into coef_grad (device, FP32, n_coefs, exchange layout) with FP32 atomics;
- * consecutive points that share a cell are first combined inside the warp.
+ *   dL/dtheta_{v,c,k} += sum_n w_i(x_n) phi_k(delta_i) dL_df[n,c]
+ *                        + sum_d dL_dgradx[n,c,d] d/dx_d (w_i phi_k(delta_i))
+ * (v the i-th corner of x_n's cell, delta_i = x_n - v in world units, phi_k
+ * the basis 1, delta_d, delta_d^2 / 2, delta_a delta_b of Eq. 1) into
+ * coef_grad (device, FP32, n_coefs, exchange layout) with FP32 reductions at
+ * L2; consecutive points that share a cell are first combined inside the
+ * warp. The summation order is not fixed, so results vary at FP32 rounding.
  * The caller zeroes coef_grad (tg_adam_step does so after using it).
  * Errors as tg_query. */
 TG_API tg_status tg_query_backward(const tg_grid *grid, const float *pts, int64_t N,
