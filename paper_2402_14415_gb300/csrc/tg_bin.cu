@@ -153,101 +153,186 @@ bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int *
     if (threadIdx.x == 0) offsets[n] = carry;
 }
 
+// Both place passes work in tiles: a tile's records are counting-sorted by
+// destination bin in shared memory, every bin reserves one run of slots, and
+// the tile is then written out in its sorted order, so that consecutive
+// threads store consecutive records of a run (coalesced lines instead of one
+// L2 request per 16-byte record).
+constexpr int kCoarseBins = kMaxSmemBins / kCoarse;          // 512
+constexpr int kCoarseTile = 4 * kHistThreads;                // records per coarse tile
+constexpr int kFineTile = 4 * kFineThreads;                  // records per fine tile
+
+struct CoarseSmem {
+    float4 stage[kCoarseTile];
+    unsigned short bin[kCoarseTile];
+    int cur[kCoarseBins];      // this chunk's next slot in every coarse bin
+    int cnt[kCoarseBins];
+    int loff[kCoarseBins];
+    int gbase[kCoarseBins];
+    int warp_tmp[32];
+};
+
+struct FineSmem {
+    float4 stage[kFineTile];
+    unsigned char brick[kFineTile];
+    int cur[kCoarse];
+    int cnt[kCoarse];
+    int loff[kCoarse];
+    int gbase[kCoarse];
+};
+
 // Coarse place: every chunk block writes its points, grouped by coarse bin
 // (kCoarse consecutive bricks), into the coarse array. A chunk's share of a
-// coarse bin is one contiguous run (hundreds of records), so the writes stream.
+// coarse bin is one contiguous run, filled tile by tile.
 __global__ void __launch_bounds__(kHistThreads)
 bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk, int res, int nbx, int nby,
                         int nbricks, const int *__restrict__ hist, const int *__restrict__ offsets,
                         float4 *__restrict__ coarse)
 {
-    __shared__ int cur[kMaxSmemBins / kCoarse];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CoarseSmem &S = *reinterpret_cast<CoarseSmem *>(smem_raw);
     const int ncoarse = (nbricks + kCoarse - 1) / kCoarse;
     const int *h = hist + (int64_t)blockIdx.x * nbricks;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int cb = wid; cb < ncoarse; cb += blockDim.x >> 5) {     // one warp per coarse bin
-        int s = 0;
+        int sum = 0;
         for (int j = lane; j < kCoarse; j += 32) {
             const int b = cb * kCoarse + j;
-            if (b < nbricks) s += __ldg(h + b);
+            if (b < nbricks) sum += __ldg(h + b);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) cur[cb] = __ldg(offsets + cb * kCoarse) + s;
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) S.cur[cb] = __ldg(offsets + cb * kCoarse) + sum;
     }
-    __syncthreads();
     const float scale = (float)(res - 1);
     const int64_t lo = (int64_t)blockIdx.x * chunk;
     const int64_t hi = min(N, lo + chunk);
-    constexpr int U = 4;   // points in flight per thread
-    for (int64_t n0 = lo + threadIdx.x; n0 < hi; n0 += (int64_t)U * blockDim.x) {
+    constexpr int U = kCoarseTile / kHistThreads;
+    for (int64_t t0 = lo; t0 < hi; t0 += kCoarseTile) {
+        const int cnt = (int)min((int64_t)kCoarseTile, hi - t0);
+        for (int j = threadIdx.x; j < ncoarse; j += blockDim.x) S.cnt[j] = 0;
+        __syncthreads();
         float x[U][3];
-        int slot[U];
+        int key[U], rank[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t n = n0 + (int64_t)u * blockDim.x;
-            if (n < hi) load_point3(pts, n, x[u]);
+            const int i = threadIdx.x + u * kHistThreads;
+            key[u] = -1;
+            if (i < cnt) load_point3(pts, t0 + i, x[u]);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t n = n0 + (int64_t)u * blockDim.x;
-            if (n < hi) {
+            const int i = threadIdx.x + u * kHistThreads;
+            if (i < cnt) {
                 int c[3];
                 float t[3];
                 locate<3>(x[u], res, scale, c, t);
-                slot[u] = atomicAdd(cur + brick_of(c, nbx, nby) / kCoarse, 1);
+                key[u] = brick_of(c, nbx, nby) / kCoarse;
+                rank[u] = atomicAdd(S.cnt + key[u], 1);
             }
         }
+        __syncthreads();
+        {   // tile offsets per bin, and one run per bin reserved from the chunk's cursor
+            const int b = threadIdx.x;
+            const int v = b < ncoarse ? S.cnt[b] : 0;
+            int total;
+            const int ex = block_exclusive_scan(v, S.warp_tmp, total);
+            if (b < ncoarse) {
+                S.loff[b] = ex;
+                S.gbase[b] = S.cur[b];
+                S.cur[b] += v;
+            }
+        }
+        __syncthreads();
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t n = n0 + (int64_t)u * blockDim.x;
-            if (n < hi) coarse[slot[u]] = make_float4(x[u][0], x[u][1], x[u][2], __int_as_float((int)n));
+            if (key[u] < 0) continue;
+            const int q = S.loff[key[u]] + rank[u];
+            S.stage[q] = make_float4(x[u][0], x[u][1], x[u][2], __int_as_float((int)(t0 + threadIdx.x + u * kHistThreads)));
+            S.bin[q] = (unsigned short)key[u];
         }
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += kHistThreads) {
+            const int bkey = S.bin[q];
+            coarse[S.gbase[bkey] + (q - S.loff[bkey])] = S.stage[q];
+        }
+        __syncthreads();
     }
 }
 
-// Fine place: one block per coarse bin scatters its records to their bricks.
-// The destination is the coarse bin's own region (about a megabyte), which
-// stays in L2 while the partial-sector writes merge.
+// Fine place: one block per coarse bin scatters its records to their bricks,
+// tile by tile, and records the permutation.
 __global__ void __launch_bounds__(kFineThreads)
 bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int nby, int nbricks,
                       const int *__restrict__ offsets, float4 *__restrict__ sorted, int *__restrict__ perm)
 {
-    __shared__ int cur[kCoarse];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FineSmem &S = *reinterpret_cast<FineSmem *>(smem_raw);
     const int b0 = blockIdx.x * kCoarse;
     const int nb = min(kCoarse, nbricks - b0);
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) cur[j] = __ldg(offsets + b0 + j);
-    __syncthreads();
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) S.cur[j] = __ldg(offsets + b0 + j);
     const int lo = __ldg(offsets + b0), hi = __ldg(offsets + b0 + nb);
     const float scale = (float)(res - 1);
-    constexpr int U = 4;
-    for (int p0 = lo + threadIdx.x; p0 < hi; p0 += U * blockDim.x) {
+    constexpr int U = kFineTile / kFineThreads;
+    const int lane = threadIdx.x & 31;
+    for (int t0 = lo; t0 < hi; t0 += kFineTile) {
+        const int cnt = min(kFineTile, hi - t0);
+        for (int j = threadIdx.x; j < kCoarse; j += blockDim.x) S.cnt[j] = 0;
+        __syncthreads();
         float4 q[U];
-        int slot[U];
+        int key[U], rank[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int p = p0 + u * blockDim.x;
-            if (p < hi) q[u] = coarse[p];
+            const int i = threadIdx.x + u * kFineThreads;
+            key[u] = -1;
+            if (i < cnt) q[u] = coarse[t0 + i];
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int p = p0 + u * blockDim.x;
-            if (p < hi) {
+            const int i = threadIdx.x + u * kFineThreads;
+            if (i < cnt) {
                 const float x[3] = {q[u].x, q[u].y, q[u].z};
                 int c[3];
                 float t[3];
                 locate<3>(x, res, scale, c, t);
-                slot[u] = atomicAdd(cur + brick_of(c, nbx, nby) - b0, 1);
+                key[u] = brick_of(c, nbx, nby) - b0;
+                rank[u] = atomicAdd(S.cnt + key[u], 1);
             }
         }
+        __syncthreads();
+        if (threadIdx.x < 32) {   // one warp: offsets of the 64 bricks in the tile, and their runs
+            const int a = S.cnt[2 * lane], b = S.cnt[2 * lane + 1];
+            int incl = a + b;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            const int ex = incl - a - b;
+            S.loff[2 * lane] = ex;
+            S.loff[2 * lane + 1] = ex + a;
+            S.gbase[2 * lane] = S.cur[2 * lane];
+            S.gbase[2 * lane + 1] = S.cur[2 * lane + 1];
+            S.cur[2 * lane] += a;
+            S.cur[2 * lane + 1] += b;
+        }
+        __syncthreads();
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int p = p0 + u * blockDim.x;
-            if (p < hi) {
-                sorted[slot[u]] = q[u];
-                perm[slot[u]] = __float_as_int(q[u].w);
-            }
+            if (key[u] < 0) continue;
+            const int p = S.loff[key[u]] + rank[u];
+            S.stage[p] = q[u];
+            S.brick[p] = (unsigned char)key[u];
         }
+        __syncthreads();
+        for (int p = threadIdx.x; p < cnt; p += kFineThreads) {
+            const int k = S.brick[p];
+            const int slot = S.gbase[k] + (p - S.loff[k]);
+            const float4 r = S.stage[p];
+            sorted[slot] = r;
+            perm[slot] = __float_as_int(r.w);
+        }
+        __syncthreads();
     }
 }
 
@@ -468,6 +553,8 @@ tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
         const int bytes = (int)(b->nbricks * sizeof(int));
         st = set_smem((const void *)bin_hist_kernel, bytes);
         if (st == TG_OK) st = set_smem((const void *)bin_chunk_scan_kernel, b->G * kColScanBricks * (int)sizeof(int));
+        if (st == TG_OK) st = set_smem((const void *)bin_coarse_place_kernel, (int)sizeof(CoarseSmem));
+        if (st == TG_OK) st = set_smem((const void *)bin_fine_place_kernel, (int)sizeof(FineSmem));
     }
     if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_batch_create");
     if (st != TG_OK) { tg_batch_destroy(b); return st; }
@@ -509,11 +596,11 @@ tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream strea
         if ((st = launch_status("tg_batch_bin: chunk scan")) != TG_OK) return st;
         bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, nullptr, nbr);
         if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;
-        bin_coarse_place_kernel<<<b->G, kHistThreads, 0, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist,
-                                                              b->offsets, b->coarse);
+        bin_coarse_place_kernel<<<b->G, kHistThreads, sizeof(CoarseSmem), s>>>(pts, N, chunk, b->res, nbx, nby, nbr,
+                                                                               b->hist, b->offsets, b->coarse);
         if ((st = launch_status("tg_batch_bin: coarse place")) != TG_OK) return st;
-        bin_fine_place_kernel<<<(nbr + kCoarse - 1) / kCoarse, kFineThreads, 0, s>>>(b->coarse, b->res, nbx, nby, nbr,
-                                                                                     b->offsets, b->sorted, b->perm);
+        bin_fine_place_kernel<<<(nbr + kCoarse - 1) / kCoarse, kFineThreads, sizeof(FineSmem), s>>>(
+            b->coarse, b->res, nbx, nby, nbr, b->offsets, b->sorted, b->perm);
         return launch_status("tg_batch_bin: fine place");
     }
     if ((st = cuda_status(cudaMemsetAsync(b->counts, 0, (b->nbricks + 1) * sizeof(int), s), "tg_batch_bin")) != TG_OK)
