@@ -66,17 +66,23 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
         __syncthreads();
         int my_lc[kPPT];
         float my_t[kPPT][3];
-        int my_n[kPPT];                              // upstream index: input index or binned slot
+        float my_u[kPPT][R::fields - 3];             // upstream gradients, loaded before the cell scan
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int i = tid + r * kBwdThreads;
             my_lc[r] = -1;
             if (i < cnt) {
                 const float4 q = sorted[base + i];
+                const int64_t n = IN_ORDER ? (int64_t)__float_as_int(q.w) : (int64_t)(base + i);
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) my_u[r][ch] = __ldg(dLdf + n * C + ch);
+                if constexpr (HAS_G) {
+#pragma unroll
+                    for (int j = 0; j < 3 * C; ++j) my_u[r][C + j] = __ldg(dLdg + n * 3 * C + j);
+                }
                 const float x[3] = {q.x, q.y, q.z};
                 int c[3];
                 locate<3>(x, res, scale, c, my_t[r]);
-                my_n[r] = IN_ORDER ? __float_as_int(q.w) : base + i;
                 my_lc[r] = (c[0] - x0) + kBrick * ((c[1] - y0) + kBrick * (c[2] - z0));
                 atomicAdd(cell_cur + my_lc[r], 1);
             }
@@ -87,15 +93,10 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
         for (int r = 0; r < kPPT; ++r) {
             if (my_lc[r] < 0) continue;
             const int pos = atomicAdd(cell_cur + my_lc[r], 1);
-            const int64_t n = my_n[r];
             float v[RS];
             v[0] = my_t[r][0]; v[1] = my_t[r][1]; v[2] = my_t[r][2];
 #pragma unroll
-            for (int ch = 0; ch < C; ++ch) v[3 + ch] = __ldg(dLdf + n * C + ch);
-            if constexpr (HAS_G) {
-#pragma unroll
-                for (int j = 0; j < 3 * C; ++j) v[3 + C + j] = __ldg(dLdg + n * 3 * C + j);
-            }
+            for (int j = 0; j < R::fields - 3; ++j) v[3 + j] = my_u[r][j];
 #pragma unroll
             for (int j = R::fields; j < RS; ++j) v[j] = 0.f;
 #pragma unroll
