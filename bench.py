@@ -8,6 +8,12 @@ A step bins the points by brick (tg_batch_bin), evaluates f at every point
 coefficients (tg_query_backward_binned). Inputs are larger than L2 (points
 201 MB, grid 671 MB, gradient 671 MB).
 
+At N = 1 the line also carries, under "configs", the other workloads of the
+method measured the same way (an SDF fit step with Adam, the query forward
+alone at orders 0-2 and FP32/BF16, a ray-marching training step, and a
+serving trace of fit jobs and queries against the same jobs run one at a
+time); --no-extras / --no-serving skip them.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs its own replica (weak scaling, no collective on
 the data path); the timed region is bracketed by barriers and the max over
@@ -297,10 +303,10 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": int(pts_np.nbytes + up_np.nbytes), "d2h_bytes_per_step": int(N * 4)},
         "gpu_launches": launches_per_step * args.steps,
     }
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and world == 1 and not args.no_extras:     # single-GPU runs only: the same on every N
         line["configs"] = {"fit_step_256_o2": bench_fit_step(), "query_only_256": bench_query_only(),
                            "render_160": bench_render()}
-        if args.serving:
+        if not args.no_serving:
             line["configs"]["serving"] = bench_serving()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, _ = oracle_sample(CPU_SAMPLE)
@@ -509,7 +515,8 @@ def profile_once():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # full-size launch captured by `ncu --set full ... python bench.py --profile`
 # (profiles/query_step_256_o2_2e24_full.md); None once the kernel has changed since.
-TRAFFIC = {"forward": None, "backward": None, "bin": None}
+TRAFFIC = {"forward": 1.200378e9 + 0.381677e9, "backward": 1.562150e9 + 0.639436e9,
+           "bin": (0.201359 + 0.003514 + 0.019937 + 0.000140 + 0.227985 + 0.222013 + 0.275145 + 0.294369) * 1e9}
 KERNEL_NAMES = {"bin": "bin_* (5 kernels, tg_batch_bin)", "forward": "brick_fwd_kernel (tg_query_binned)",
                 "backward": "brick_bwd_kernel (tg_query_backward_binned)"}
 
@@ -522,7 +529,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the fit / query-only / render lines")
-    ap.add_argument("--serving", action="store_true", help="also run the serving trace (about a minute)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving trace (about 25 s)")
     ap.add_argument("--profile", action="store_true",
                     help="run each kernel of the step once, untimed (for ncu captures)")
     ap.add_argument("--profile-points", type=int, default=N_POINTS)
