@@ -108,7 +108,9 @@ typedef struct {
 TG_API tg_status tg_get_info(const tg_grid *grid, tg_grid_info *info);
 
 /* Load FP32 coefficients (device, exchange layout, n_coefs floats) into the
- * master copy and the stored copy (rounded to the storage dtype). */
+ * master copy and the stored copy (rounded to the storage dtype). `src` may be
+ * the grid's own master (tg_grid_info.master), e.g. after an optimiser outside
+ * the library updated it in place: then only the stored copy is refreshed. */
 TG_API tg_status tg_set_coefs(tg_grid *grid, const float *src, tg_stream stream);
 
 /* Read coefficients into `dst` (device, n_coefs floats). which = 0: the
@@ -329,6 +331,19 @@ TG_API tg_status tg_render_rays(const tg_grid *density, const tg_grid *color, co
                                 const float *rays_d, int64_t R, int S, uint64_t seed, uint64_t ray_base,
                                 float bg, float *rgb_out, const float *target_rgb, tg_batch *batch,
                                 float *density_grad, float *color_grad, float *loss_sum, tg_stream stream);
+
+/* Backward of tg_render_rays for any upstream dL_drgb (device, R x 3), e.g.
+ * from a loss computed outside the library. Recomputes every sample of every
+ * ray - the same stratified samples as the forward for the same seed,
+ * ray_base and bg, so nothing is stored between the two calls - and ADDS
+ *   dL/dtheta = sum_r sum_a dL_drgb[r, a] dC_a(r)/dtheta
+ * into density_grad and color_grad under the same rules as the training form
+ * of tg_render_rays (batch, dtypes, orders). rgb_out may be NULL; otherwise
+ * it receives the recomputed colours. */
+TG_API tg_status tg_render_rays_backward(const tg_grid *density, const tg_grid *color, const float *rays_o,
+                                         const float *rays_d, int64_t R, int S, uint64_t seed, uint64_t ray_base,
+                                         float bg, const float *dL_drgb, tg_batch *batch, float *density_grad,
+                                         float *color_grad, float *rgb_out, tg_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Fit / query server (continuous batching; no paper counterpart - the paper

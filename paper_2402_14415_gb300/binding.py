@@ -103,6 +103,8 @@ _SIGS = {
     "tg_server_set_policy": [_vp, _int],
     "tg_render_rays": [_vp, _vp, _vp, _vp, _i64, _int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_float, _vp, _vp,
                        _vp, _vp, _vp, _vp, _vp],
+    "tg_render_rays_backward": [_vp, _vp, _vp, _vp, _i64, _int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_float,
+                                _vp, _vp, _vp, _vp, _vp, _vp],
 }
 
 
@@ -426,6 +428,22 @@ def tg_render_rays(density: Grid, color: Grid, rays_o, rays_d, S: int, seed: int
                                  _ptr(loss_sum, "loss_sum", optional=True), _stream(stream)), "tg_render_rays")
     if batch is not None and target is not None:
         batch.n = R * S
+    return out
+
+
+def tg_render_rays_backward(density: Grid, color: Grid, rays_o, rays_d, dL_drgb, S: int, batch: Batch,
+                            density_grad, color_grad, seed: int = 0, ray_base: int = 0, bg: float = 1.0, out=None,
+                            stream=None):
+    """Adds dL/dtheta of both grids for an upstream dL/drgb, recomputing every sample of the forward."""
+    R = rays_o.shape[0]
+    _check(load().tg_render_rays_backward(density.handle, color.handle, _ptr(rays_o, "rays_o", numel=3 * R),
+                                          _ptr(rays_d, "rays_d", numel=3 * R), R, S, seed, ray_base, bg,
+                                          _ptr(dL_drgb, "dL_drgb", numel=3 * R), batch.handle,
+                                          _ptr(density_grad, "density_grad", numel=density.n_coefs),
+                                          _ptr(color_grad, "color_grad", numel=color.n_coefs),
+                                          _ptr(out, "out", numel=3 * R, optional=True), _stream(stream)),
+           "tg_render_rays_backward")
+    batch.n = R * S
     return out
 
 

@@ -204,8 +204,10 @@ tg_status tg_set_coefs(tg_grid *g, const float *src, tg_stream stream)
 {
     if (!g || !src) return fail(TG_EINVAL, "tg_set_coefs: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    tg_status st = cuda_status(cudaMemcpyAsync(g->master, src, (size_t)g->ncoef * 4, cudaMemcpyDeviceToDevice, s),
-                               "tg_set_coefs: copy");
+    tg_status st = TG_OK;
+    if (src != g->master)      // src may be the master itself: then only the stored copy is refreshed
+        st = cuda_status(cudaMemcpyAsync(g->master, src, (size_t)g->ncoef * 4, cudaMemcpyDeviceToDevice, s),
+                         "tg_set_coefs: copy");
     if (st != TG_OK || g->dtype == TG_F32) return st;
     unsigned nb = elementwise_blocks(g->ncoef);
     if (g->dtype == TG_BF16) narrow_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(g->master, nullptr, (__nv_bfloat16 *)g->store, g->ncoef);

@@ -86,8 +86,8 @@ template <typename TD, typename TC, int OD, int OC>
 __global__ void __launch_bounds__(256)
 render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int res, const float *__restrict__ ro,
               const float *__restrict__ rd, int64_t R, int S, uint64_t seed, uint64_t ray_base, float bg,
-              float *__restrict__ rgb, const float *__restrict__ target, float inv_r, float *__restrict__ loss,
-              float *__restrict__ xs, float *__restrict__ ud, float *__restrict__ uc)
+              float *__restrict__ rgb, const float *__restrict__ target, const float *__restrict__ dldc, float inv_r,
+              float *__restrict__ loss, float *__restrict__ xs, float *__restrict__ ud, float *__restrict__ uc)
 {
     const int lane = threadIdx.x & 31;
     const int m = (S + 31) / 32;                 // samples per lane
@@ -145,19 +145,23 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
         float Cr[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) Cr[a] = warp_sum(acc[a]) + T_end * bg;
-        if (lane == 0) {
+        if (lane == 0 && rgb) {
             rgb[3 * r] = Cr[0]; rgb[3 * r + 1] = Cr[1]; rgb[3 * r + 2] = Cr[2];
         }
-        if (!target) continue;
-        // Eq. 11: L = (1/R) sum_r ||C_r - C*_r||^2, dL/dC = 2 (C - C*) / R
+        if (!target && !dldc) continue;
+        // dL/dC: given (dldc), or of Eq. 11, L = (1/R) sum_r ||C_r - C*_r||^2, dL/dC = 2 (C - C*) / R
         float g[3], l = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float e = Cr[a] - target[3 * r + a];
-            g[a] = 2.f * e * inv_r;
-            l += e * e;
+            if (dldc) {
+                g[a] = dldc[3 * r + a];
+            } else {
+                const float e = Cr[a] - target[3 * r + a];
+                g[a] = 2.f * e * inv_r;
+                l += e * e;
+            }
         }
-        if (lane == 0) atomicAdd(loss, l);
+        if (target && lane == 0) atomicAdd(loss, l);
         // P_i = sum_{j<=i} T_j alpha_j c_j: lane-exclusive prefix + in-lane running sum
         float pre[3];
 #pragma unroll
@@ -194,28 +198,28 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
 
 using namespace tg;
 
-extern "C" tg_status tg_render_rays(const tg_grid *dg, const tg_grid *cg, const float *rays_o, const float *rays_d,
-                                    int64_t R, int S, uint64_t seed, uint64_t ray_base, float bg, float *rgb_out,
-                                    const float *target_rgb, tg_batch *batch, float *density_grad, float *color_grad,
-                                    float *loss_sum, tg_stream stream)
+static tg_status render_impl(const tg_grid *dg, const tg_grid *cg, const float *rays_o, const float *rays_d,
+                             int64_t R, int S, uint64_t seed, uint64_t ray_base, float bg, float *rgb_out,
+                             const float *target_rgb, const float *dldc, tg_batch *batch, float *density_grad,
+                             float *color_grad, float *loss_sum, cudaStream_t s, const char *who)
 {
-    if (!dg || !cg) return fail(TG_EINVAL, "tg_render_rays: NULL grid");
+    if (!dg || !cg) return fail(TG_EINVAL, "%s: NULL grid", who);
     if (dg->dim != 3 || cg->dim != 3 || dg->C != 1 || cg->C != 3)
-        return fail(TG_EINVAL, "tg_render_rays: needs a 3-D 1-channel density grid and a 3-D 3-channel colour grid");
-    if (dg->res != cg->res) return fail(TG_EINVAL, "tg_render_rays: the two grids must share res");
-    if (R < 0 || S < 1 || S > 32 * kMaxSamplesPerLane) return fail(TG_EINVAL, "tg_render_rays: R >= 0, 1 <= S <= 512");
+        return fail(TG_EINVAL, "%s: needs a 3-D 1-channel density grid and a 3-D 3-channel colour grid", who);
+    if (dg->res != cg->res) return fail(TG_EINVAL, "%s: the two grids must share res", who);
+    if (R < 0 || S < 1 || S > 32 * kMaxSamplesPerLane) return fail(TG_EINVAL, "%s: R >= 0, 1 <= S <= 512", who);
     if (R == 0) return TG_OK;
-    if (!rays_o || !rays_d || !rgb_out) return fail(TG_EINVAL, "tg_render_rays: NULL ray or output pointer");
-    cudaStream_t s = (cudaStream_t)stream;
+    if (!rays_o || !rays_d || (!rgb_out && !dldc)) return fail(TG_EINVAL, "%s: NULL ray or output pointer", who);
     tg_status st;
     const int64_t NS = R * S;
+    const bool train = target_rgb || dldc;
     float *xs = nullptr, *ud = nullptr, *uc = nullptr;
-    if (target_rgb) {
-        if (!batch || !density_grad || !color_grad || !loss_sum)
-            return fail(TG_EINVAL, "tg_render_rays: training needs batch, both gradients and loss_sum");
-        if ((st = check_pair(dg, batch, "tg_render_rays")) != TG_OK) return st;
-        if (NS > batch->max_points) return fail(TG_EINVAL, "tg_render_rays: R * S exceeds the batch's max_points");
-        if ((st = ensure_aux(batch, 7 * NS, "tg_render_rays")) != TG_OK) return st;
+    if (train) {
+        if (!batch || !density_grad || !color_grad || (target_rgb && !loss_sum))
+            return fail(TG_EINVAL, "%s: the backward needs batch and both gradients (and loss_sum with a target)", who);
+        if ((st = check_pair(dg, batch, who)) != TG_OK) return st;
+        if (NS > batch->max_points) return fail(TG_EINVAL, "%s: R * S exceeds the batch's max_points", who);
+        if ((st = ensure_aux(batch, 7 * NS, who)) != TG_OK) return st;
         xs = batch->aux; ud = batch->aux + 3 * NS; uc = batch->aux + 4 * NS;
     }
     const int warps_per_block = 8;
@@ -226,23 +230,43 @@ extern "C" tg_status tg_render_rays(const tg_grid *dg, const tg_grid *cg, const 
 #define TG_RK(TD, TC, OD, OC)                                                                              \
     render_kernel<TD, TC, OD, OC><<<nb, 256, 0, s>>>((const TD *)dg->store, (const TC *)cg->store, dg->res, \
                                                      rays_o, rays_d, R, S, seed, ray_base, bg, rgb_out,       \
-                                                     target_rgb, inv_r, loss_sum, xs, ud, uc)
+                                                     target_rgb, dldc, inv_r, loss_sum, xs, ud, uc)
     const int key = dg->order * 10 + cg->order;
     if (dg->dtype == TG_F32 && cg->dtype == TG_F32) {
         if (key == 21) TG_RK(float, float, 2, 1); else if (key == 0) TG_RK(float, float, 0, 0);
         else if (key == 20) TG_RK(float, float, 2, 0); else if (key == 11) TG_RK(float, float, 1, 1);
-        else return fail(TG_EINVAL, "tg_render_rays: unsupported order pair %d/%d", dg->order, cg->order);
+        else return fail(TG_EINVAL, "%s: unsupported order pair %d/%d", who, dg->order, cg->order);
     } else if (dg->dtype == TG_BF16 && cg->dtype == TG_BF16) {
         if (key == 21) TG_RK(__nv_bfloat16, __nv_bfloat16, 2, 1); else if (key == 0) TG_RK(__nv_bfloat16, __nv_bfloat16, 0, 0);
         else if (key == 20) TG_RK(__nv_bfloat16, __nv_bfloat16, 2, 0); else if (key == 11) TG_RK(__nv_bfloat16, __nv_bfloat16, 1, 1);
-        else return fail(TG_EINVAL, "tg_render_rays: unsupported order pair %d/%d", dg->order, cg->order);
+        else return fail(TG_EINVAL, "%s: unsupported order pair %d/%d", who, dg->order, cg->order);
     } else {
-        return fail(TG_EINVAL, "tg_render_rays: both grids must be FP32 or both BF16");
+        return fail(TG_EINVAL, "%s: both grids must be FP32 or both BF16", who);
     }
 #undef TG_RK
-    if ((st = launch_status("tg_render_rays")) != TG_OK || !target_rgb) return st;
+    if ((st = launch_status(who)) != TG_OK || !train) return st;
     // coefficient gradients of both grids through the binned backward
-    if ((st = tg_batch_bin(batch, xs, NS, stream)) != TG_OK) return st;
-    if ((st = tg_query_backward_binned(dg, batch, ud, nullptr, density_grad, TG_ORDER_INPUT, stream)) != TG_OK) return st;
-    return tg_query_backward_binned(cg, batch, uc, nullptr, color_grad, TG_ORDER_INPUT, stream);
+    if ((st = tg_batch_bin(batch, xs, NS, s)) != TG_OK) return st;
+    if ((st = tg_query_backward_binned(dg, batch, ud, nullptr, density_grad, TG_ORDER_INPUT, s)) != TG_OK) return st;
+    return tg_query_backward_binned(cg, batch, uc, nullptr, color_grad, TG_ORDER_INPUT, s);
+}
+
+extern "C" tg_status tg_render_rays(const tg_grid *dg, const tg_grid *cg, const float *rays_o, const float *rays_d,
+                                    int64_t R, int S, uint64_t seed, uint64_t ray_base, float bg, float *rgb_out,
+                                    const float *target_rgb, tg_batch *batch, float *density_grad, float *color_grad,
+                                    float *loss_sum, tg_stream stream)
+{
+    if (!rgb_out && R > 0) return fail(TG_EINVAL, "tg_render_rays: rgb_out is NULL");
+    return render_impl(dg, cg, rays_o, rays_d, R, S, seed, ray_base, bg, rgb_out, target_rgb, nullptr, batch,
+                       density_grad, color_grad, loss_sum, (cudaStream_t)stream, "tg_render_rays");
+}
+
+extern "C" tg_status tg_render_rays_backward(const tg_grid *dg, const tg_grid *cg, const float *rays_o,
+                                             const float *rays_d, int64_t R, int S, uint64_t seed, uint64_t ray_base,
+                                             float bg, const float *dL_drgb, tg_batch *batch, float *density_grad,
+                                             float *color_grad, float *rgb_out, tg_stream stream)
+{
+    if (!dL_drgb && R > 0) return fail(TG_EINVAL, "tg_render_rays_backward: dL_drgb is NULL");
+    return render_impl(dg, cg, rays_o, rays_d, R, S, seed, ray_base, bg, rgb_out, nullptr, dL_drgb, batch,
+                       density_grad, color_grad, nullptr, (cudaStream_t)stream, "tg_render_rays_backward");
 }
