@@ -531,6 +531,9 @@ def profile_once():
     # spatial-gradient variants of the two brick kernels
     tg.tg_query_binned(g, batch, out=out, grad_x=gx)
     tg.tg_query_backward_binned(g, batch, U, grad, dL_dgradx=UG)
+    # the point-parallel pair on the same unsorted points (no binning; warp-aggregated FP32 reductions)
+    tg.tg_query(g, P, out=out)
+    tg.tg_query_backward(g, P, U, grad)
     tg.tg_adam_step(g, grad, lr=1e-3, step=1)
     torch.cuda.synchronize()
     print("profile pass done, timeouts:", tg.tg_batch_timeouts(batch))
