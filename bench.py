@@ -329,6 +329,7 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0 and world == 1 and not args.no_extras:     # single-GPU runs only: the same on every N
         line["configs"] = {"fit_step_256_o2": bench_fit_step(), "query_only_256": bench_query_only(),
+                           "query_pair_c_abi_256": bench_query_pair(),
                            "render_160": bench_render()}
         if not args.no_serving:
             line["configs"]["serving"] = bench_serving()
@@ -405,6 +406,36 @@ def bench_query_only(steps=5, warmup=2):
             del g
     return {"workload": "query forward (bin + binned forward, input order), 256^3, 2^24 uniform points",
             "unit": "Mpts/s", **res}
+
+
+def bench_query_pair(steps=5, warmup=2):
+    """The C-ABI pair tg_query + tg_query_backward on 2^24 uniform points at 256^3 order 2 FP32: each call
+    bins into the grid's own batch (large 3-D batches) - against the point-parallel kernels on the same points."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    n = N_POINTS
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    P = torch.rand((n, 3), device="cuda", generator=gen)
+    U = torch.randn((n, 1), device="cuda", generator=gen)
+    out = torch.empty((n, 1), device="cuda")
+    g = tg.tg_create(3, RES, ORDER, 1, "f32", seed=0, init_std=1.0)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+
+    def pair():
+        tg.tg_query(g, P, out=out)
+        tg.tg_query_backward(g, P, U, grad)
+    ms = _time_ms(pair, steps, warmup)
+    chunk = (1 << 18) - 1                 # below the binning threshold: the point-parallel kernels
+
+    def pair_pp():
+        for i in range(0, n, chunk):
+            tg.tg_query(g, P[i:i + chunk], out=out[i:i + chunk])
+            tg.tg_query_backward(g, P[i:i + chunk], U[i:i + chunk], grad)
+    ms_pp = _time_ms(pair_pp, 2, 1)
+    return {"workload": "tg_query + tg_query_backward, 256^3 order 2 FP32, 2^24 uniform points", "unit": "Mpts/s",
+            "binned_by_the_calls": round(n / (ms * 1e-3) / 1e6, 1), "ms": round(ms, 3),
+            "point_parallel": round(n / (ms_pp * 1e-3) / 1e6, 1), "ms_point_parallel": round(ms_pp, 3)}
 
 
 def bench_render(steps=5, warmup=2):

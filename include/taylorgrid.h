@@ -133,8 +133,15 @@ TG_API tg_status tg_locate(int dim, int res, const float *pts, int64_t N, int32_
  * gradient in world units (device, N x channels x dim) = d f / d x, which is
  * the blend derivative of Eq. 4 plus the series derivative g + H delta of
  * each corner, times (res - 1). Points are clamped to the domain.
+ * Large 3-D batches (N >= 2^18 and at least 8 points per 8^3-cell brick on
+ * average, on a grid the binned calls below accept, outside stream capture)
+ * are binned into a batch the grid owns and evaluated by the binned kernels;
+ * the first such call allocates that batch (36 bytes per point, synchronously)
+ * and later larger calls grow it. Calls on one grid from several streams are
+ * ordered through an event; the results equal the point-parallel ones up to
+ * FP32 rounding. Everything else runs one thread per point.
  * N = 0 is a no-op. Errors: TG_EINVAL (NULL grid/pts/out with N > 0,
- * N < 0), TG_EDEVICE (launch failure). */
+ * N < 0), TG_ENOMEM, TG_EDEVICE (launch failure). */
 TG_API tg_status tg_query(const tg_grid *grid, const float *pts, int64_t N,
                    float *out, float *grad_x, tg_stream stream);
 
@@ -149,6 +156,8 @@ TG_API tg_status tg_query(const tg_grid *grid, const float *pts, int64_t N,
  * coef_grad (device, FP32, n_coefs, exchange layout) with FP32 reductions at
  * L2; consecutive points that share a cell are first combined inside the
  * warp. The summation order is not fixed, so results vary at FP32 rounding.
+ * Large batches are binned as in tg_query (when coef_grad is 16-byte
+ * aligned) and scattered by the binned backward.
  * The caller zeroes coef_grad (tg_adam_step does so after using it).
  * Errors as tg_query. */
 TG_API tg_status tg_query_backward(const tg_grid *grid, const float *pts, int64_t N,

@@ -450,6 +450,49 @@ tg_status check_pair(const tg_grid *g, const tg_batch *bt, const char *who)
     return TG_OK;
 }
 
+bool auto_bin_wanted(const tg_grid *g, int64_t N, const float *coef_grad, cudaStream_t s)
+{
+    if (g->dim != 3 || N < kAutoBinMin) return false;
+    const int64_t nb = (int64_t)((g->res - 2) / kBrick + 1);
+    if (N < 8 * nb * nb * nb) return false;
+    const int nv = g->K * g->C, elem = g->dtype == TG_F32 ? 4 : 2;
+    if (((int64_t)g->res * nv * elem) % 16 != 0 || ((int64_t)g->res * nv * 4) % 16 != 0) return false;
+    if (box_inner_host(nv, elem) > 256 || box_inner_host(nv, 4) > 256) return false;
+    if (coef_grad && ((uintptr_t)coef_grad & 15) != 0) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone;
+}
+
+tg_status with_auto_batch(const tg_grid *gc, const float *pts, int64_t N, cudaStream_t s,
+                          tg_status (*op)(const tg_grid *, tg_batch *, void *, cudaStream_t), void *arg)
+{
+    static std::mutex mu;      // host-side bookkeeping and enqueueing only
+    std::lock_guard<std::mutex> lock(mu);
+    tg_grid *g = const_cast<tg_grid *>(gc);
+    tg_status st = TG_OK;
+    if (!g->auto_event &&
+        (st = cuda_status(cudaEventCreateWithFlags(&g->auto_event, cudaEventDisableTiming), "query: binning event")) != TG_OK)
+        return st;
+    if (!g->auto_batch || g->auto_batch->max_points < N) {
+        if (g->auto_batch) {
+            cudaEventSynchronize(g->auto_event);
+            tg_batch_destroy(g->auto_batch);
+            g->auto_batch = nullptr;
+        }
+        if ((st = tg_batch_create(3, g->res, N, &g->auto_batch)) != TG_OK) return st;
+    }
+    if ((st = cuda_status(cudaStreamWaitEvent(s, g->auto_event, 0), "query: order the binning scratch")) != TG_OK)
+        return st;
+    st = tg_batch_bin(g->auto_batch, pts, N, s);
+    if (st == TG_OK) st = op(gc, g->auto_batch, arg, s);
+    const tg_status rec = cuda_status(cudaEventRecord(g->auto_event, s), "query: binning event");
+    return st != TG_OK ? st : rec;
+}
+
 static unsigned grid_for(const void *kernel, int threads, int64_t N)
 {
     int64_t need = (N + threads - 1) / threads;

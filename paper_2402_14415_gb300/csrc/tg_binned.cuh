@@ -68,4 +68,18 @@ tg_status check_pair(const tg_grid *g, const tg_batch *bt, const char *who);
 tg_status ensure_stage(tg_batch *bt, int64_t floats, const char *who);
 tg_status ensure_aux(tg_batch *bt, int64_t floats, const char *who);
 
+// Large 3-D batches of tg_query / tg_query_backward are binned into a
+// grid-owned batch and served by the binned kernels (input order).
+// auto_bin_wanted: at least kAutoBinMin points and 8 per brick on average, a
+// grid the binned path accepts (with FP32 gradients for the backward, which
+// must be 16-byte aligned), and a stream that is not capturing.
+constexpr int64_t kAutoBinMin = (int64_t)1 << 18;
+bool auto_bin_wanted(const tg_grid *g, int64_t N, const float *coef_grad, cudaStream_t s);
+// Bins pts into the grid's batch (creating or growing it: a synchronous
+// allocation), runs op(batch) on stream s and orders the batch's next use after
+// this one with an event. Calls on one grid from several threads are
+// serialised on the host; their GPU work is ordered through the event.
+tg_status with_auto_batch(const tg_grid *g, const float *pts, int64_t N, cudaStream_t s,
+                          tg_status (*op)(const tg_grid *, tg_batch *, void *, cudaStream_t), void *arg);
+
 }  // namespace tg

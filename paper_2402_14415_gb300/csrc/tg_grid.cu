@@ -178,6 +178,9 @@ tg_status tg_create(int dim, int res, int order, int channels, tg_dtype dtype, u
 tg_status tg_destroy(tg_grid *g)
 {
     if (!g) return TG_OK;
+    if (g->auto_event) cudaEventSynchronize(g->auto_event);
+    if (g->auto_batch) tg_batch_destroy(g->auto_batch);
+    if (g->auto_event) cudaEventDestroy(g->auto_event);
     if (g->store && g->store != g->master) cudaFree(g->store);
     if (g->master) cudaFree(g->master);
     if (g->adam_m) cudaFree(g->adam_m);

@@ -20,6 +20,8 @@ struct tg_grid {
     float *master;       // FP32 master copy
     float *adam_m;       // Adam first moment (lazily allocated)
     float *adam_v;       // Adam second moment
+    struct tg_batch *auto_batch;   // binning scratch of large tg_query / tg_query_backward calls (lazy)
+    cudaEvent_t auto_event;        // last use of auto_batch
 };
 
 namespace tg {
@@ -34,6 +36,13 @@ tg_status launch_status(const char *what);
 int num_sms();                      // SM count of the current device (cached per device)
 // Resident blocks per SM of a kernel at a launch shape (cached per device and kernel).
 int blocks_per_sm(const void *kernel, int threads, size_t smem);
+
+// The point-parallel query pair (one thread per point; tg_query.cu). tg_query /
+// tg_query_backward use them for small, 2-D or captured batches.
+tg_status query_point_parallel(const tg_grid *g, const float *pts, int64_t N, float *out, float *grad_x,
+                               cudaStream_t s);
+tg_status query_backward_point_parallel(const tg_grid *g, const float *pts, int64_t N, const float *dL_df,
+                                        const float *dL_dgradx, float *coef_grad, cudaStream_t s);
 
 // Adam over all coefficients (tg_adam.cu); with step_dev != nullptr the
 // 0-based step index is read on the device and prm->step is ignored.

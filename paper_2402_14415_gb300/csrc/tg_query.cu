@@ -1,4 +1,7 @@
-// C ABI of the point-parallel query path (tg_query / tg_query_backward).
+// C ABI of the query pair (tg_query / tg_query_backward): the point-parallel
+// kernels, or, for large 3-D batches, binning into a grid-owned batch and the
+// brick-binned kernels.
+#include "tg_binned.cuh"
 #include "tg_query.cuh"
 
 namespace tg {
@@ -37,6 +40,49 @@ static tg_status bwd(const tg_grid *g, const float *pts, int64_t N, const float 
 
 using namespace tg;
 
+namespace tg {
+
+tg_status query_point_parallel(const tg_grid *g, const float *pts, int64_t N, float *out, float *grad_x,
+                               cudaStream_t s)
+{
+#define TG_Q(D, O, C)                                                                                          \
+    (g->dtype == TG_F32    ? QueryLaunch<float>::fwd<D, O, C>(g, pts, N, out, grad_x, s)                       \
+     : g->dtype == TG_BF16 ? QueryLaunch<__nv_bfloat16>::fwd<D, O, C>(g, pts, N, out, grad_x, s)               \
+                           : QueryLaunch<__half>::fwd<D, O, C>(g, pts, N, out, grad_x, s))
+    return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_Q);
+#undef TG_Q
+}
+
+tg_status query_backward_point_parallel(const tg_grid *g, const float *pts, int64_t N, const float *dL_df,
+                                        const float *dL_dgradx, float *coef_grad, cudaStream_t s)
+{
+#define TG_B(D, O, C) bwd<D, O, C>(g, pts, N, dL_df, dL_dgradx, coef_grad, s)
+    return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_B);
+#undef TG_B
+}
+
+struct FwdArgs {
+    float *out, *grad_x;
+};
+struct BwdArgs {
+    const float *dL_df, *dL_dgradx;
+    float *coef_grad;
+};
+
+static tg_status binned_fwd_op(const tg_grid *g, tg_batch *bt, void *a, cudaStream_t s)
+{
+    const FwdArgs *f = static_cast<const FwdArgs *>(a);
+    return tg_query_binned(g, bt, f->out, f->grad_x, TG_ORDER_INPUT, s);
+}
+
+static tg_status binned_bwd_op(const tg_grid *g, tg_batch *bt, void *a, cudaStream_t s)
+{
+    const BwdArgs *b = static_cast<const BwdArgs *>(a);
+    return tg_query_backward_binned(g, bt, b->dL_df, b->dL_dgradx, b->coef_grad, TG_ORDER_INPUT, s);
+}
+
+}  // namespace tg
+
 extern "C" {
 
 tg_status tg_query(const tg_grid *g, const float *pts, int64_t N, float *out, float *grad_x, tg_stream stream)
@@ -46,12 +92,11 @@ tg_status tg_query(const tg_grid *g, const float *pts, int64_t N, float *out, fl
     if (N == 0) return TG_OK;
     if (!pts || !out) return fail(TG_EINVAL, "tg_query: NULL pts or out");
     cudaStream_t s = (cudaStream_t)stream;
-#define TG_Q(D, O, C)                                                                                          \
-    (g->dtype == TG_F32    ? QueryLaunch<float>::fwd<D, O, C>(g, pts, N, out, grad_x, s)                       \
-     : g->dtype == TG_BF16 ? QueryLaunch<__nv_bfloat16>::fwd<D, O, C>(g, pts, N, out, grad_x, s)               \
-                           : QueryLaunch<__half>::fwd<D, O, C>(g, pts, N, out, grad_x, s))
-    return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_Q);
-#undef TG_Q
+    if (auto_bin_wanted(g, N, nullptr, s)) {
+        FwdArgs a{out, grad_x};
+        return with_auto_batch(g, pts, N, s, binned_fwd_op, &a);
+    }
+    return query_point_parallel(g, pts, N, out, grad_x, s);
 }
 
 tg_status tg_query_backward(const tg_grid *g, const float *pts, int64_t N, const float *dL_df,
@@ -62,9 +107,11 @@ tg_status tg_query_backward(const tg_grid *g, const float *pts, int64_t N, const
     if (N == 0) return TG_OK;
     if (!pts || !dL_df || !coef_grad) return fail(TG_EINVAL, "tg_query_backward: NULL pts, dL_df or coef_grad");
     cudaStream_t s = (cudaStream_t)stream;
-#define TG_B(D, O, C) bwd<D, O, C>(g, pts, N, dL_df, dL_dgradx, coef_grad, s)
-    return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_B);
-#undef TG_B
+    if (auto_bin_wanted(g, N, coef_grad, s)) {
+        BwdArgs a{dL_df, dL_dgradx, coef_grad};
+        return with_auto_batch(g, pts, N, s, binned_bwd_op, &a);
+    }
+    return query_backward_point_parallel(g, pts, N, dL_df, dL_dgradx, coef_grad, s);
 }
 
 }  // extern "C"

@@ -359,7 +359,8 @@ tg_status tg_server_step(tg_server *s, int *pending)
             }
             j->event = nullptr;
             tg_status st = cuda_status(cudaEventCreateWithFlags(&j->event, cudaEventDisableTiming), "server: event");
-            if (st == TG_OK) st = tg_query(g->grid, j->qpts, j->qn, j->qout, nullptr, g->stream);
+            // point-parallel: no binning scratch outside the admission budget
+            if (st == TG_OK) st = query_point_parallel(g->grid, j->qpts, j->qn, j->qout, nullptr, g->stream);
             if (st == TG_OK) st = cuda_status(cudaEventRecord(j->event, g->stream), "server: query event");
             j->t_start = s->now();
             j->state = st == TG_OK ? TG_JOB_RUNNING : TG_JOB_FAILED;

@@ -160,3 +160,46 @@ def test_init_matches_generator(tg):
     got = tg.tg_get_coefs(g, which=1).cpu().numpy()
     want = W.init_coefs(3, 6, 2, 1, seed=42, std=0.01)
     np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-9)
+
+
+@pytest.mark.parametrize("order,C", [(2, 1), (1, 3)])
+def test_large_batches_take_the_binned_path(tg, order, C):
+    """N >= 2^18 on a 3-D grid: tg_query / tg_query_backward bin into the grid's own batch; the
+    results match the oracle and the point-parallel kernels (the same points in chunks below 2^18)."""
+    res, N = 34, 300000
+    coefs = W.init_coefs(3, res, order, C, seed=8, std=0.5)
+    g = tg.tg_create(3, res, order, C, "f32")
+    tg.tg_set_coefs(g, to_dev(coefs))
+    pts = np.concatenate([points(3, res, N - 1000, seed=31), W.uniform_points(32, 1000)])
+    N = pts.shape[0]                       # the helper adds the edge cases
+    P = to_dev(pts)
+    out, gx = tg.tg_query(g, P, want_grad=True)
+    chunks = [tg.tg_query(g, P[i:i + 100000], want_grad=True) for i in range(0, N, 100000)]
+    torch.cuda.synchronize()
+    check_forward(out.cpu().numpy(), gx.cpu().numpy(), 3, res, order, C, coefs.astype(np.float64), pts)
+    torch.testing.assert_close(out, torch.cat([c[0] for c in chunks]), rtol=1e-5, atol=1e-5)
+    up = np.random.default_rng(3).normal(size=(N, C)).astype(np.float32)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward(g, P, to_dev(up), grad)
+    ref = torch.zeros(g.n_coefs, device="cuda")
+    for i in range(0, N, 100000):
+        tg.tg_query_backward(g, P[i:i + 100000], to_dev(up[i:i + 100000]), ref)
+    torch.cuda.synchronize()
+    check_coef_grad(grad.cpu().numpy(), 3, res, order, C, pts, up)
+    torch.testing.assert_close(grad, ref, rtol=1e-4, atol=1e-4 * float(ref.abs().max()))
+
+
+def test_large_batches_on_two_streams_share_the_grid_batch(tg):
+    res, N = 34, 1 << 18
+    g = tg.tg_create(3, res, 2, 1, "f32", seed=4, init_std=0.5)
+    Ps = [to_dev(W.uniform_points(40 + k, N)) for k in range(2)]
+    refs = [torch.cat([tg.tg_query(g, P[i:i + 65536]) for i in range(0, N, 65536)]) for P in Ps]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    outs = []
+    for rep in range(3):
+        for P, s in zip(Ps, streams):
+            outs.append(tg.tg_query(g, P, stream=s))
+    torch.cuda.synchronize()
+    for k, o in enumerate(outs):
+        torch.testing.assert_close(o, refs[k % 2], rtol=1e-5, atol=1e-5)
