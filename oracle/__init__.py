@@ -56,7 +56,9 @@ def lib():
             L.tgo_query_absscale.argtypes = [i32, i32, i32, i32, _f64p, i64, _f32p, _f64p]
             L.tgo_adam.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64]
             L.tgo_sdf_union.argtypes = [i32, _f32p, i32, _f32p, _f64p]; L.tgo_sdf_union.restype = f64
-            L.tgo_sdf_step.argtypes = [i32, i32, _f64p, i64, _f32p, i32, _f32p, i32, _f32p, f64, _f64p, _f64p]
+            L.tgo_sdf_step.argtypes = [i32, i32, _f64p, i64, _f32p, i32, _f32p, i32, _f32p, f64, f64, _f64p, _f64p]
+            L.tgo_adaptive_weight1.argtypes = [f64, f64]; L.tgo_adaptive_weight1.restype = f64
+            L.tgo_tv.argtypes = [i32, i32, _f64p, f64, _f64p]; L.tgo_tv.restype = f64
             L.tgo_uniform.argtypes = [u64, u64, u64]; L.tgo_uniform.restype = f64
             L.tgo_ray_box.argtypes = [_f64p, _f64p, _f64p, _f64p]; L.tgo_ray_box.restype = i32
             L.tgo_render.argtypes = [i32, i32, _f64p, i32, _f64p, i64, i32, _f32p, _f32p, u64, u64, f64,
@@ -147,16 +149,30 @@ def sdf_union(spheres, boxes, x):
                                          _p(x[n], _f64p)) for n in range(x.shape[0])])
 
 
-def sdf_step(res, order, coefs, pts, spheres, boxes, lambda_eik):
-    """One SDF fitting step; returns (coef_grad, (L1, eikonal mean))."""
+def sdf_step(res, order, coefs, pts, spheres, boxes, lambda_eik, k_weight=0.0):
+    """One SDF fitting step (Eq. 6 with Eq. 7's weight for k_weight > 0, plus the eikonal term);
+    returns (coef_grad, (weighted reconstruction mean, eikonal mean))."""
     pts = _c(pts, np.float32).reshape(-1, 3)
     sph = _c(spheres, np.float32).reshape(-1); box = _c(boxes, np.float32).reshape(-1)
     K = num_coefs(3, order)
     g = np.zeros(res ** 3 * K); loss = np.zeros(3)
     lib().tgo_sdf_step(res, order, _p(_c(coefs, np.float64), _f64p), pts.shape[0], _p(pts, _f32p),
-                       len(sph) // 4, _p(sph, _f32p), len(box) // 6, _p(box, _f32p), lambda_eik,
+                       len(sph) // 4, _p(sph, _f32p), len(box) // 6, _p(box, _f32p), lambda_eik, k_weight,
                        _p(g, _f64p), _p(loss, _f64p))
     return g, (loss[0], loss[1])
+
+
+def adaptive_weight1(k, z) -> float:
+    """w'(z) of Eq. 7 (1 for k <= 0)."""
+    return lib().tgo_adaptive_weight1(k, z)
+
+
+def tv(res, nv, coefs, lam=1.0, want_grad=True):
+    """Total variation term of Sec. 3.2 over a 3-D grid ([vertex][nv] coefficients): (L_TV, lam * dL_TV/dtheta)."""
+    c = _c(coefs, np.float64)
+    g = np.zeros(res ** 3 * nv) if want_grad else None
+    L = lib().tgo_tv(res, nv, _p(c, _f64p), lam, _p(g, _f64p) if want_grad else None)
+    return L, g
 
 
 def uniform(seed, stream, idx) -> float:

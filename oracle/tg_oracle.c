@@ -332,16 +332,29 @@ TGO_API double tgo_sdf_union(int ns, const float *sph, int nb, const float *box,
     return best;
 }
 
+/* The adaptive weight of Eq. 7: w'(z) = 1 - |2 sigmoid(k z) - 1|, which is 1
+ * at z = 0 and falls towards 0 away from the surface; k <= 0 turns the
+ * weighting off (w' = 1). */
+TGO_API double tgo_adaptive_weight1(double k, double z)
+{
+    if (!(k > 0.0)) return 1.0;
+    return 1.0 - fabs(2.0 / (1.0 + exp(-k * z)) - 1.0);
+}
+
 /* One SDF fitting step on given points (Sec. 3.2):
- *   L = mean_P |f(x) - d(x)|                        (Eq. 6 with w = 1)
+ *   L = mean_P w(x) |f(x) - d(x)|                   (Eq. 6; w of Eq. 7)
  *     + lambda_eik * mean_P (||grad_x f(x)|| - 1)^2  (IGR eikonal term, Eq. 8)
- * with d evaluated at the clamped point. The gradient of L with respect to
- * the coefficients is accumulated into coef_grad. loss[0] = L1 term,
- * loss[1] = eikonal mean (unweighted), loss[2] = mean |f - d| (same as loss[0]).
- * sign(0) = 0; a zero spatial gradient (norm < 1e-12) gets zero eikonal grad. */
+ * with w(x) = max(w'(f(x)), w'(d(x))) and d evaluated at the clamped point.
+ * w only weights the residual: it is held fixed in the gradient (a weight
+ * that followed f would reward pushing f away from the surface). With k <= 0,
+ * w = 1 and the first term is the plain L1 loss. The gradient of L with
+ * respect to the coefficients is accumulated into coef_grad. loss[0] = the
+ * weighted reconstruction term, loss[1] = eikonal mean (unweighted),
+ * loss[2] = mean |f - d|. sign(0) = 0; a zero spatial gradient
+ * (norm < 1e-12) gets zero eikonal gradient. */
 TGO_API void tgo_sdf_step(int res, int order, const double *coefs, int64_t N, const float *pts,
                           int ns, const float *sph, int nb, const float *box,
-                          double lambda_eik, double *coef_grad, double *loss)
+                          double lambda_eik, double k_weight, double *coef_grad, double *loss)
 {
     const int dim = 3;
     double *f = (double *)malloc(sizeof(double) * N);
@@ -349,22 +362,64 @@ TGO_API void tgo_sdf_step(int res, int order, const double *coefs, int64_t N, co
     double *dLdf = (double *)malloc(sizeof(double) * N);
     double *dLdg = (double *)malloc(sizeof(double) * N * 3);
     tgo_query(dim, res, order, 1, coefs, N, pts, f, gx, NULL, NULL);
-    double l1 = 0, eik = 0;
+    double rec = 0, l1 = 0, eik = 0;
     for (int64_t n = 0; n < N; ++n) {
         double x[3];
         for (int a = 0; a < 3; ++a) x[a] = fmin(fmax((double)pts[n * 3 + a], 0.0), 1.0);
         double d = tgo_sdf_union(ns, sph, nb, box, x);
         double r = f[n] - d;
+        double w = fmax(tgo_adaptive_weight1(k_weight, f[n]), tgo_adaptive_weight1(k_weight, d));
+        rec += w * fabs(r);
         l1 += fabs(r);
-        dLdf[n] = (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (double)N;
+        dLdf[n] = w * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (double)N;
         double nrm = sqrt(gx[3 * n] * gx[3 * n] + gx[3 * n + 1] * gx[3 * n + 1] + gx[3 * n + 2] * gx[3 * n + 2]);
         eik += (nrm - 1.0) * (nrm - 1.0);
         for (int a = 0; a < 3; ++a)
             dLdg[3 * n + a] = nrm < 1e-12 ? 0.0 : lambda_eik * 2.0 * (nrm - 1.0) * gx[3 * n + a] / nrm / (double)N;
     }
     tgo_query_backward(dim, res, order, 1, N, pts, dLdf, lambda_eik != 0.0 ? dLdg : NULL, coef_grad, NULL);
-    if (loss) { loss[0] = l1 / (double)N; loss[1] = eik / (double)N; loss[2] = l1 / (double)N; }
+    if (loss) { loss[0] = rec / (double)N; loss[1] = eik / (double)N; loss[2] = l1 / (double)N; }
     free(f); free(gx); free(dLdf); free(dLdg);
+}
+
+/* Total variation term of Sec. 3.2, in the form of Plenoxels, over a 3-D grid
+ * of res^3 vertices with nv coefficients each (layout [vertex][nv]): for every
+ * vertex v and coefficient c,
+ *   n(v, c) = sqrt(D_x^2 + D_y^2 + D_z^2),  D_a = theta(v + e_a, c) - theta(v, c)
+ * (D_a = 0 where v + e_a lies outside the grid), and
+ *   L_TV = (1 / res^3) sum_{v, c} n(v, c).
+ * Adds lambda * dL_TV/dtheta into coef_grad (when not NULL) and returns L_TV.
+ * Where n = 0 the term contributes no gradient. */
+TGO_API double tgo_tv(int res, int nv, const double *coefs, double lambda, double *coef_grad)
+{
+    const int64_t V = (int64_t)res * res * res;
+    const double inv_v = 1.0 / (double)V;
+    double total = 0.0;
+    for (int64_t z = 0; z < res; ++z)
+        for (int64_t y = 0; y < res; ++y)
+            for (int64_t x = 0; x < res; ++x) {
+                const int64_t v = x + res * (y + res * z);
+                const int64_t nbr[3] = {x + 1 < res ? v + 1 : -1, y + 1 < res ? v + res : -1,
+                                        z + 1 < res ? v + (int64_t)res * res : -1};
+                for (int c = 0; c < nv; ++c) {
+                    const double t0 = coefs[v * nv + c];
+                    double D[3], n2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        D[a] = nbr[a] >= 0 ? coefs[nbr[a] * nv + c] - t0 : 0.0;
+                        n2 += D[a] * D[a];
+                    }
+                    const double n = sqrt(n2);
+                    total += n;
+                    if (!coef_grad || n == 0.0) continue;
+                    const double s = lambda * inv_v / n;       /* d n / d D_a = D_a / n */
+                    for (int a = 0; a < 3; ++a) {
+                        if (nbr[a] < 0) continue;
+                        coef_grad[nbr[a] * nv + c] += s * D[a];
+                        coef_grad[v * nv + c] -= s * D[a];
+                    }
+                }
+            }
+    return total * inv_v;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -375,6 +375,79 @@ def test_sdf_step_loss_values():
     assert eik < 1e-10
 
 
+def test_adaptive_weight_closed_form():
+    """Eq. 7: w'(z) = 1 - |2 sigmoid(k z) - 1| = 1 - tanh(|k z| / 2); 1 on the surface, even in z, towards 0 away."""
+    for k in (10.0, 100.0):
+        for z in (-0.3, -0.01, 0.0, 0.004, 0.2):
+            assert abs(oracle.adaptive_weight1(k, z) - (1 - math.tanh(abs(k * z) / 2))) < 1e-14
+    assert oracle.adaptive_weight1(100.0, 0.0) == 1.0
+    assert oracle.adaptive_weight1(100.0, 1.0) < 1e-40
+    assert oracle.adaptive_weight1(0.0, 0.7) == 1.0 and oracle.adaptive_weight1(-3.0, 0.7) == 1.0
+
+
+def test_adaptive_weight_k0_is_plain_l1_and_weighted_step_matches_fixed_weight_fd():
+    r = rng(82)
+    res, order = 3, 2
+    coefs = r.normal(size=res ** 3 * 10) * 0.2
+    shape = W.sphere_shape((0.45, 0.5, 0.55), 0.3)
+    pts = r.random((64, 3)).astype(np.float32)
+    g0, (l0, _) = oracle.sdf_step(res, order, coefs, pts, shape.spheres, shape.boxes, 0.0)
+    gk0, (lk0, _) = oracle.sdf_step(res, order, coefs, pts, shape.spheres, shape.boxes, 0.0, k_weight=0.0)
+    assert l0 == lk0
+    np.testing.assert_allclose(g0, gk0, rtol=1e-12, atol=1e-18)     # the oracle's OpenMP sums vary in the last bits
+    k = 20.0
+    g, (lw, _) = oracle.sdf_step(res, order, coefs, pts, shape.spheres, shape.boxes, 0.0, k_weight=k)
+    # the weight is held at its value for the current coefficients
+    f0, _, _, _ = oracle.query(3, res, order, 1, coefs, pts, want_grad=False)
+    d = oracle.sdf_union(shape.spheres, shape.boxes, np.clip(pts.astype(np.float64), 0, 1))
+    w = np.maximum([oracle.adaptive_weight1(k, v) for v in f0[:, 0]], [oracle.adaptive_weight1(k, v) for v in d])
+    assert w.min() < 0.9 and abs(lw - np.mean(w * np.abs(f0[:, 0] - d))) < 1e-12
+
+    def L(c):
+        f, _, _, _ = oracle.query(3, res, order, 1, c, pts, want_grad=False)
+        return np.mean(w * np.abs(f[:, 0] - d))
+
+    eps = 1e-6
+    for j in r.choice(coefs.size, 40, replace=False):
+        e = np.zeros_like(coefs); e[j] = eps
+        fd = (L(coefs + e) - L(coefs - e)) / (2 * eps)
+        assert abs(fd - g[j]) < 1e-7 + 1e-5 * abs(fd), (j, fd, g[j])
+
+
+def test_tv_constant_and_ramp_closed_forms():
+    res, nv = 6, 3
+    const = np.tile(np.array([0.3, -1.0, 2.0]), res ** 3)
+    L, g = oracle.tv(res, nv, const)
+    assert L == 0.0 and not g.any()
+    # theta(v, 0) = a i along x, other channels zero: n = |a| except on the last x plane
+    a = -0.7
+    i = np.arange(res ** 3) % res
+    ramp = np.zeros((res ** 3, nv)); ramp[:, 0] = a * i
+    L, g = oracle.tv(res, nv, ramp.ravel(), lam=2.0)
+    np.testing.assert_allclose(L, (res - 1) * res * res * abs(a) / res ** 3, rtol=1e-14)
+    g = g.reshape(-1, nv)
+    want = np.zeros(res ** 3)
+    want[i == 0] = -np.sign(a) * 2.0 / res ** 3        # only the first and last planes keep a gradient
+    want[i == res - 1] = np.sign(a) * 2.0 / res ** 3
+    np.testing.assert_allclose(g[:, 0], want, atol=1e-15)
+    assert not g[:, 1:].any()
+
+
+def test_tv_gradient_finite_differences_and_channel_separability():
+    r = rng(83)
+    res, nv = 4, 2
+    c = r.normal(size=res ** 3 * nv)
+    L, g = oracle.tv(res, nv, c, lam=0.5)
+    L0, _ = oracle.tv(res, 1, c.reshape(-1, nv)[:, 0].copy(), want_grad=False)
+    L1, _ = oracle.tv(res, 1, c.reshape(-1, nv)[:, 1].copy(), want_grad=False)
+    np.testing.assert_allclose(L, L0 + L1, rtol=1e-13)
+    eps = 1e-6
+    for j in r.choice(c.size, 40, replace=False):
+        e = np.zeros_like(c); e[j] = eps
+        fd = 0.5 * (oracle.tv(res, nv, c + e, want_grad=False)[0] - oracle.tv(res, nv, c - e, want_grad=False)[0]) / (2 * eps)
+        assert abs(fd - g[j]) < 1e-8 + 1e-6 * abs(fd), (j, fd, g[j])
+
+
 # --------------------------------------------------------------------------
 # Volume rendering (Sec. 3.3, Eq. 10 / Eq. 11)
 # --------------------------------------------------------------------------
