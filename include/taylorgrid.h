@@ -296,19 +296,32 @@ TG_API tg_status tg_sample_sdf_points(const tg_shape *shape, uint64_t seed, int6
                                       float jitter, float *pts, tg_stream stream);
 
 /* One SDF fitting step on a 3-D one-channel grid (Sec. 3.2):
- *   L = mean_P |f(x) - d(x)|  +  lambda_eik * mean_P (||grad_x f(x)|| - 1)^2
- * (Eq. 6 with w = 1, IGR's eikonal term of Eq. 8). The points are `pts`
+ *   L = mean_P w(x) |f(x) - d(x)|  +  lambda_eik * mean_P (||grad_x f(x)|| - 1)^2
+ * (Eq. 6, IGR's eikonal term of Eq. 8) with Eq. 7's adaptive weight
+ *   w(x) = max(w'(f(x)), w'(d(x))),  w'(z) = 1 - |2 sigmoid(k_weight z) - 1|
+ * held fixed in the gradient (k_weight <= 0: w = 1, the plain L1 loss; the
+ * paper leaves k open). Add the total variation term with tg_tv_step. The points are `pts`
  * (device, N x 3) or, if pts is NULL, the fit batch of (seed, step) drawn on
  * the device. The points are binned into `batch` (created for the grid's
  * res, max_points >= N), the forward, the per-point loss and the backward run
  * in binned order, and dL/dtheta is ADDED to coef_grad (device, n_coefs).
- * loss_sums (device, 2 floats, accumulated) receives sum |f - d| and
+ * loss_sums (device, 2 floats, accumulated) receives sum w |f - d| and
  * sum (||grad_x f|| - 1)^2 over the batch. sign(0) = 0; points whose spatial
  * gradient has norm below 1e-12 get no eikonal gradient.
  * The first call may grow the batch's staging buffer (11 floats per point). */
 TG_API tg_status tg_sdf_step(const tg_grid *grid, tg_batch *batch, const tg_shape *shape, const float *pts,
-                             int64_t N, uint64_t seed, int64_t step, float lambda_eik, float *coef_grad,
-                             float *loss_sums, tg_stream stream);
+                             int64_t N, uint64_t seed, int64_t step, float lambda_eik, float k_weight,
+                             float *coef_grad, float *loss_sums, tg_stream stream);
+
+/* Total variation term of Sec. 3.2 (the form of Plenoxels) on a 3-D grid's
+ * FP32 master, over every vertex v and coefficient c of the exchange layout:
+ *   n(v, c) = sqrt(D_x^2 + D_y^2 + D_z^2),  D_a = theta(v + e_a, c) - theta(v, c)
+ * (D_a = 0 where v + e_a is outside the grid), L_TV = sum_{v,c} n(v, c) / res^3.
+ * ADDS lambda * dL_TV/dtheta into coef_grad (device, FP32, n_coefs; a zero n
+ * contributes nothing) and, if loss_sum (device, 1 float) is not NULL, adds
+ * sum_{v,c} n(v, c) to it. One pass over the grid (a 3-D stencil).
+ * Errors: TG_EINVAL (NULL grid or coef_grad, 2-D grid, lambda < 0), TG_EDEVICE. */
+TG_API tg_status tg_tv_step(const tg_grid *grid, float lambda, float *coef_grad, float *loss_sum, tg_stream stream);
 
 /* Accumulates sum_P |f(x) - d(x)| over N points (device, N x 3) into
  * err_sum (device, 1 float): the mean |SDF error| of a fit is err_sum / N.
@@ -384,6 +397,8 @@ typedef struct {
     int max_steps;
     float tol;                  /* stop once the evaluated mean |SDF error| < tol */
     float lr, lambda_eik, init_std;
+    float k_weight;             /* Eq. 7 adaptive weight (tg_sdf_step); <= 0: off */
+    float lambda_tv;            /* total variation weight (tg_tv_step); 0: off */
 } tg_fit_desc;
 
 typedef enum { TG_JOB_QUEUED = 0, TG_JOB_RUNNING = 1, TG_JOB_DONE = 2, TG_JOB_FAILED = 3 } tg_job_state;

@@ -51,7 +51,7 @@ class FitDesc(ctypes.Structure):
                 ("n_spheres", _int), ("n_boxes", _int), ("spheres", _vp), ("boxes", _vp), ("area_cdf", _vp),
                 ("points_per_step", _i64), ("eval_points", _i64), ("eval_every", _int), ("max_steps", _int),
                 ("tol", ctypes.c_float), ("lr", ctypes.c_float), ("lambda_eik", ctypes.c_float),
-                ("init_std", ctypes.c_float)]
+                ("init_std", ctypes.c_float), ("k_weight", ctypes.c_float), ("lambda_tv", ctypes.c_float)]
 
 
 class JobResult(ctypes.Structure):
@@ -89,8 +89,9 @@ _SIGS = {
     "tg_adam_step": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
     "tg_sdf_eval_target": [ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
     "tg_sample_sdf_points": [ctypes.POINTER(ShapeStruct), ctypes.c_uint64, _i64, _i64, ctypes.c_float, _vp, _vp],
-    "tg_sdf_step": [_vp, _vp, ctypes.POINTER(ShapeStruct), _vp, _i64, ctypes.c_uint64, _i64, ctypes.c_float, _vp,
-                    _vp, _vp],
+    "tg_sdf_step": [_vp, _vp, ctypes.POINTER(ShapeStruct), _vp, _i64, ctypes.c_uint64, _i64, ctypes.c_float,
+                    ctypes.c_float, _vp, _vp, _vp],
+    "tg_tv_step": [_vp, ctypes.c_float, _vp, _vp, _vp],
     "tg_sdf_error": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
     "tg_server_create": [ctypes.c_size_t, _int, ctypes.POINTER(_vp)],
     "tg_server_destroy": [_vp],
@@ -395,13 +396,19 @@ def tg_sample_sdf_points(shape: DeviceShape, seed: int, step: int, n: int, jitte
 
 
 def tg_sdf_step(grid: Grid, batch: Batch, shape: DeviceShape, coef_grad, loss_sums, pts=None, n=None, seed=0,
-                step=0, lambda_eik=0.0, stream=None):
+                step=0, lambda_eik=0.0, k_weight=0.0, stream=None):
     n = pts.shape[0] if pts is not None else n
     _check(load().tg_sdf_step(grid.handle, batch.handle, ctypes.byref(shape.struct),
                               None if pts is None else _ptr(pts, "pts", numel=3 * n), n, seed, step, lambda_eik,
-                              _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), _ptr(loss_sums, "loss_sums", numel=2),
-                              _stream(stream)), "tg_sdf_step")
+                              k_weight, _ptr(coef_grad, "coef_grad", numel=grid.n_coefs),
+                              _ptr(loss_sums, "loss_sums", numel=2), _stream(stream)), "tg_sdf_step")
     batch.n = n
+
+
+def tg_tv_step(grid: Grid, lam: float, coef_grad, loss_sum=None, stream=None):
+    """Adds lam * dL_TV/dtheta (Sec. 3.2's total variation term) into coef_grad; sum of n(v, c) into loss_sum."""
+    _check(load().tg_tv_step(grid.handle, lam, _ptr(coef_grad, "coef_grad", numel=grid.n_coefs),
+                             _ptr(loss_sum, "loss_sum", optional=True), _stream(stream)), "tg_tv_step")
 
 
 def tg_sdf_error(grid: Grid, shape: DeviceShape, pts, err_sum=None, stream=None):
@@ -463,14 +470,15 @@ class Server:
 
     def fit_job(self, shape_spheres, shape_boxes, area_cdf, res, order=2, dtype="f32", seed=0, points_per_step=1 << 16,
                 eval_points=1 << 16, eval_every=10, max_steps=1000, tol=2e-3, lr=5e-3, lambda_eik=0.0,
-                init_std=1e-3) -> int:
+                init_std=1e-3, k_weight=0.0, lambda_tv=0.0) -> int:
         import numpy as np
         sph = np.ascontiguousarray(shape_spheres, np.float32).reshape(-1)
         box = np.ascontiguousarray(shape_boxes, np.float32).reshape(-1)
         cdf = np.ascontiguousarray(area_cdf, np.float32).reshape(-1)
         d = FitDesc(res, order, DTYPES[dtype] if isinstance(dtype, str) else dtype, seed, sph.size // 4, box.size // 6,
                     sph.ctypes.data if sph.size else None, box.ctypes.data if box.size else None, cdf.ctypes.data,
-                    points_per_step, eval_points, eval_every, max_steps, tol, lr, lambda_eik, init_std)
+                    points_per_step, eval_points, eval_every, max_steps, tol, lr, lambda_eik, init_std, k_weight,
+                    lambda_tv)
         jid = _i64()
         _check(load().tg_fit_job(self._h, ctypes.byref(d), ctypes.byref(jid)), "tg_fit_job")
         return jid.value

@@ -133,7 +133,7 @@ __device__ __forceinline__ float block_sum(float v, float *tmp)
 // an eikonal weight, dL/d(grad_x f) = lambda 2 (|g| - 1) g / |g| / N.
 __global__ void __launch_bounds__(256)
 sdf_loss_kernel(ShapeView s, const float4 *__restrict__ sorted, int64_t N, const float *__restrict__ f,
-                const float *__restrict__ g, float lambda, float inv_n, float *__restrict__ uf,
+                const float *__restrict__ g, float lambda, float k_weight, float inv_n, float *__restrict__ uf,
                 float *__restrict__ ug, float *__restrict__ sums)
 {
     __shared__ float tmp[32];
@@ -142,8 +142,15 @@ sdf_loss_kernel(ShapeView s, const float4 *__restrict__ sorted, int64_t N, const
         const float4 q = sorted[p];
         const float d = sdf_union(s, clamp01(q.x), clamp01(q.y), clamp01(q.z));
         const float r = f[p] - d;
-        l1 += fabsf(r);
-        uf[p] = r > 0.f ? inv_n : (r < 0.f ? -inv_n : 0.f);
+        // Eq. 7: w = max(w'(f), w'(d)), w'(z) = 1 - |2 sigmoid(k z) - 1| = 2 e / (1 + e), e = exp(-|k z|);
+        // a fixed weight of the residual (k <= 0: w = 1)
+        float w = 1.f;
+        if (k_weight > 0.f) {
+            const float ef = expf(-fabsf(k_weight * f[p])), ed = expf(-fabsf(k_weight * d));
+            w = fmaxf(2.f * ef / (1.f + ef), 2.f * ed / (1.f + ed));
+        }
+        l1 += w * fabsf(r);
+        uf[p] = r > 0.f ? w * inv_n : (r < 0.f ? -w * inv_n : 0.f);
         if (g) {
             const float gx = g[3 * p], gy = g[3 * p + 1], gz = g[3 * p + 2];
             const float e = sqrtf(gx * gx + gy * gy + gz * gz);
@@ -200,8 +207,8 @@ static unsigned blocks_for(int64_t n, int per_sm = 8)
 }
 
 tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, const float *pts, int64_t N,
-                        uint64_t seed, int64_t step, const int64_t *step_dev, float lambda_eik, float *coef_grad,
-                        float *loss_sums, cudaStream_t cs)
+                        uint64_t seed, int64_t step, const int64_t *step_dev, float lambda_eik, float k_weight,
+                        float *coef_grad, float *loss_sums, cudaStream_t cs)
 {
     tg_status st;
     if ((st = ensure_stage(bt, 11 * N, "tg_sdf_step")) != TG_OK) return st;
@@ -215,7 +222,7 @@ tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, cons
     }
     if ((st = tg_batch_bin(bt, pts, N, cs)) != TG_OK) return st;
     if ((st = tg_query_binned(g, bt, f, eik ? gx : nullptr, TG_ORDER_BINNED, cs)) != TG_OK) return st;
-    sdf_loss_kernel<<<blocks_for(N), 256, 0, cs>>>(s, bt->sorted, N, f, eik ? gx : nullptr, lambda_eik,
+    sdf_loss_kernel<<<blocks_for(N), 256, 0, cs>>>(s, bt->sorted, N, f, eik ? gx : nullptr, lambda_eik, k_weight,
                                                    1.0f / (float)N, uf, ug, loss_sums);
     if ((st = launch_status("tg_sdf_step: loss")) != TG_OK) return st;
     return tg_query_backward_binned(g, bt, uf, eik ? ug : nullptr, coef_grad, TG_ORDER_BINNED, cs);
@@ -270,7 +277,7 @@ tg_status tg_sample_sdf_points(const tg_shape *shape, uint64_t seed, int64_t ste
 }
 
 tg_status tg_sdf_step(const tg_grid *g, tg_batch *bt, const tg_shape *shape, const float *pts, int64_t N,
-                      uint64_t seed, int64_t step, float lambda_eik, float *coef_grad, float *loss_sums,
+                      uint64_t seed, int64_t step, float lambda_eik, float k_weight, float *coef_grad, float *loss_sums,
                       tg_stream stream)
 {
     ShapeView s;
@@ -282,7 +289,8 @@ tg_status tg_sdf_step(const tg_grid *g, tg_batch *bt, const tg_shape *shape, con
     if (!coef_grad || !loss_sums) return fail(TG_EINVAL, "tg_sdf_step: NULL coef_grad or loss_sums");
     if (!pts && !s.cdf) return fail(TG_EINVAL, "tg_sdf_step: sampling needs area_cdf");
     if (!(lambda_eik >= 0.f)) return fail(TG_EINVAL, "tg_sdf_step: lambda_eik must be >= 0");
-    return sdf_step_impl(g, bt, s, pts, N, seed, step, nullptr, lambda_eik, coef_grad, loss_sums, (cudaStream_t)stream);
+    return sdf_step_impl(g, bt, s, pts, N, seed, step, nullptr, lambda_eik, k_weight, coef_grad, loss_sums,
+                         (cudaStream_t)stream);
 }
 
 tg_status tg_sdf_error(const tg_grid *g, const tg_shape *shape, const float *pts, int64_t N, float *err_sum,

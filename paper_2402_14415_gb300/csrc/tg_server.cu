@@ -131,8 +131,9 @@ static tg_status record_step(Job *j)
 {
     const tg_fit_desc &d = j->desc;
     tg_status st = sdf_step_impl(j->grid, j->batch, j->sv, nullptr, d.points_per_step, d.seed, 0, j->step(),
-                                 d.lambda_eik, j->grad, j->loss(), j->stream);
+                                 d.lambda_eik, d.k_weight, j->grad, j->loss(), j->stream);
     if (st != TG_OK) return st;
+    if (d.lambda_tv > 0.f && (st = tg_tv_step(j->grid, d.lambda_tv, j->grad, nullptr, j->stream)) != TG_OK) return st;
     tg_adam prm{d.lr, 0.9f, 0.999f, 1e-8f, 1};
     if ((st = adam_launch(j->grid, j->grad, &prm, j->step(), j->stream)) != TG_OK) return st;
     eval_gate_kernel<<<1, 1, 0, j->stream>>>(j->step(), d.eval_every, j->gate());

@@ -22,8 +22,10 @@ class FitResult:
 
 def fit_sdf(grid: tg.Grid, shape: tg.DeviceShape, steps: int, n_points: int, lr: float, lambda_eik: float = 0.0,
             seed: int = 1, eval_pts: torch.Tensor | None = None, eval_every: int = 0, tol: float = 0.0,
-            points_fn=None, log_every: int = 0, stream=None) -> FitResult:
-    """Runs up to `steps` Adam steps of the SDF loss.
+            points_fn=None, log_every: int = 0, k_weight: float = 0.0, lambda_tv: float = 0.0,
+            stream=None) -> FitResult:
+    """Runs up to `steps` Adam steps of the SDF loss (Eq. 8 of Sec. 3.2: the reconstruction term of Eq. 6 with
+    Eq. 7's weight when k_weight > 0, lambda_eik times the eikonal term, lambda_tv times the TV term).
 
     points_fn(step) -> (n, 3) device tensor overrides the device sampler (used
     to feed both the library and the oracle the same batches). With tol > 0
@@ -39,7 +41,9 @@ def fit_sdf(grid: tg.Grid, shape: tg.DeviceShape, steps: int, n_points: int, lr:
         if log_every and k % log_every == 0:
             loss.zero_()
         tg.tg_sdf_step(grid, batch, shape, grad, loss, pts=pts, n=n_points, seed=seed, step=k,
-                       lambda_eik=lambda_eik, stream=stream)
+                       lambda_eik=lambda_eik, k_weight=k_weight, stream=stream)
+        if lambda_tv > 0:
+            tg.tg_tv_step(grid, lambda_tv, grad, stream=stream)
         tg.tg_adam_step(grid, grad, lr=lr, step=k + 1, stream=stream)
         res.steps = k + 1
         if log_every and k % log_every == 0:

@@ -34,8 +34,8 @@ def test_device_sampler_matches_generator(tg, shape_fn):
     assert close.mean() > 0.999
 
 
-@pytest.mark.parametrize("lam", [0.0, 0.1])
-def test_sdf_step_matches_oracle(tg, lam):
+@pytest.mark.parametrize("lam,k", [(0.0, 0.0), (0.1, 0.0), (0.1, 50.0)])
+def test_sdf_step_matches_oracle(tg, lam, k):
     res, order = 34, 2
     shape = W.union_shape(0)
     coefs = W.init_coefs(3, res, order, 1, seed=4, std=0.05)
@@ -45,10 +45,10 @@ def test_sdf_step_matches_oracle(tg, lam):
     batch = tg.tg_batch_create(3, res, pts.shape[0])
     grad = torch.zeros(g.n_coefs, device="cuda")
     loss = torch.zeros(2, device="cuda")
-    tg.tg_sdf_step(g, batch, dev_shape(tg, shape), grad, loss, pts=to_dev(pts), lambda_eik=lam)
+    tg.tg_sdf_step(g, batch, dev_shape(tg, shape), grad, loss, pts=to_dev(pts), lambda_eik=lam, k_weight=k)
     torch.cuda.synchronize()
     c64 = coefs.astype(np.float64)
-    ref, (l1, eik) = oracle.sdf_step(res, order, c64, pts, shape.spheres, shape.boxes, lam)
+    ref, (l1, eik) = oracle.sdf_step(res, order, c64, pts, shape.spheres, shape.boxes, lam, k_weight=k)
     N = pts.shape[0]
     np.testing.assert_allclose(loss[0].item() / N, l1, rtol=1e-5)
     if lam > 0:
@@ -107,3 +107,42 @@ def test_fit_low_precision_storage_tracks_fp32(tg):
     assert errs["f32"] < start / 3, (errs, start)
     for dt in ["bf16", "f16"]:
         assert errs[dt] <= 1.05 * errs["f32"], errs
+
+
+@pytest.mark.parametrize("res,order,C", [(5, 2, 1), (37, 2, 1), (40, 1, 3), (33, 0, 2)])
+def test_tv_step_matches_oracle(tg, res, order, C):
+    """The TV term and its gradient (tiles of 32 x 8 x 32 vertices with ragged edges) against the oracle."""
+    K = (1, 4, 10)[order]
+    coefs = W.init_coefs(3, res, order, C, seed=12, std=0.3)
+    g = tg.tg_create(3, res, order, C, "f32")
+    tg.tg_set_coefs(g, to_dev(coefs))
+    lam = 0.7
+    start = np.random.default_rng(5).normal(size=g.n_coefs).astype(np.float32)
+    grad = to_dev(start)
+    loss = torch.zeros(1, device="cuda")
+    tg.tg_tv_step(g, lam, grad, loss)
+    torch.cuda.synchronize()
+    L, ref = oracle.tv(res, K * C, coefs.astype(np.float64), lam=lam)
+    np.testing.assert_allclose(loss.item() / res ** 3, L, rtol=1e-4)
+    got = grad.cpu().numpy().astype(np.float64) - start
+    # each entry is lam / res^3 times a sum of at most four unit-bounded terms
+    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-5 * 4 * lam / res ** 3 + 1e-6 * np.abs(start).max())
+
+
+def test_fit_with_the_papers_full_objective(tg):
+    """Eq. 6-8 with Eq. 7's weight (k = 100), lambda_1 = 1e-4, lambda_2 = 2e-5 (the paper's weights), lr 3e-3."""
+    res, n, steps = 64, 1 << 16, 400
+    shape = W.union_shape(0)
+    dshape = dev_shape(tg, shape)
+    eval_pts = to_dev(W.sdf_points(shape, seed=2, step=0, n=1 << 16))
+    g = tg.tg_create(3, res, 2, 1, "f32", seed=0, init_std=1e-3)
+    r = fit_sdf(g, dshape, steps=steps, n_points=n, lr=3e-3, lambda_eik=1e-4, k_weight=100.0, lambda_tv=2e-5,
+                eval_pts=eval_pts)
+    ev = eval_pts.cpu().numpy()
+    start = np.abs(shape.sdf(ev)).mean()
+    assert r.final_error < start / 2, (r.final_error, start)
+    # Eq. 7 concentrates the fit on the surface: the near-surface half of the evaluation points
+    near = eval_pts[eval_pts.shape[0] // 2:].contiguous()
+    err = tg.tg_sdf_error(g, dshape, near).item() / near.shape[0]
+    start_near = np.abs(shape.sdf(ev[ev.shape[0] // 2:])).mean()
+    assert err < start_near / 4, (err, start_near)

@@ -115,3 +115,14 @@ def test_smallest_first_admission(tg):
     # one slot, all four queued before the first tick: small, then mid (and its query once its grid exists), then big
     assert r[small]["t_start"] <= r[small]["t_done"] <= r[mid]["t_start"] <= r[q]["t_start"]
     assert r[mid]["t_done"] <= r[big]["t_start"]
+
+
+def test_fit_job_with_weight_and_tv(tg):
+    srv = tg.Server(budget_bytes=8 << 30)
+    jid = srv.fit_job(*shape_args(W.sphere_shape()), res=32, order=2, points_per_step=1 << 14, eval_points=1 << 14,
+                      eval_every=10, max_steps=200, tol=3e-3, lr=1e-2, lambda_eik=1e-4, k_weight=50.0, lambda_tv=2e-5)
+    srv.run_until_idle(timeout_s=120)
+    r = srv.poll(jid)
+    # Eq. 7 leaves the far field loose, so the mixed evaluation points stop short of tol: all 200 steps run
+    start = float(np.abs(W.sphere_shape().sdf(W.sdf_points(W.sphere_shape(), seed=1, step=0, n=1 << 14))).mean())
+    assert r["state"] == "done" and r["steps"] == 200 and 0 <= r["error"] < start / 2, (r, start)
