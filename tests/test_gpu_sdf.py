@@ -109,7 +109,8 @@ def test_fit_low_precision_storage_tracks_fp32(tg):
         assert errs[dt] <= 1.05 * errs["f32"], errs
 
 
-@pytest.mark.parametrize("res,order,C", [(5, 2, 1), (37, 2, 1), (40, 1, 3), (33, 0, 2)])
+@pytest.mark.parametrize("res,order,C", [(5, 2, 1), (37, 2, 1), (40, 1, 3), (33, 0, 2), (6, 0, 1), (7, 0, 3),
+                                         (64, 2, 2)])
 def test_tv_step_matches_oracle(tg, res, order, C):
     """The TV term and its gradient (tiles of 32 x 8 x 32 vertices with ragged edges) against the oracle."""
     K = (1, 4, 10)[order]
