@@ -117,6 +117,18 @@ TG_API tg_status tg_set_coefs(tg_grid *grid, const float *src, tg_stream stream)
  * stored copy, widened to FP32 (what queries use); which = 1: the FP32 master. */
 TG_API tg_status tg_get_coefs(const tg_grid *grid, float *dst, int which, tg_stream stream);
 
+/* Checkpoint / resume (synchronous; host files). tg_save writes the grid's
+ * shape, its FP32 master coefficients and, if the grid has taken an Adam
+ * step, Adam's two moments: format "TGCK", u32 version 1, i32 dim, res,
+ * order, channels, dtype, has_adam, i64 n_coefs, then n_coefs floats per
+ * array (little-endian). tg_load creates a grid on the current device from
+ * such a file (the stored BF16/FP16 copy is rounded from the master), so a fit
+ * resumes where it stopped; the caller keeps its own Adam step counter.
+ * Errors: TG_EINVAL (NULL argument, unreadable / malformed / truncated file),
+ * TG_ENOMEM, TG_EDEVICE. */
+TG_API tg_status tg_save(const tg_grid *grid, const char *path);
+TG_API tg_status tg_load(const char *path, tg_grid **out);
+
 /* ---------------------------------------------------------------------------
  * Field query, Eq. 2 - Eq. 4.
  * ------------------------------------------------------------------------ */
@@ -328,6 +340,14 @@ TG_API tg_status tg_tv_step(const tg_grid *grid, float lambda, float *coef_grad,
  * 3-D one-channel grids. */
 TG_API tg_status tg_sdf_error(const tg_grid *grid, const tg_shape *shape, const float *pts, int64_t N,
                               float *err_sum, tg_stream stream);
+
+/* Volumetric IoU of the fitted shape (the paper's reconstruction metric,
+ * measured on points instead of meshes): over N points (device, N x 3) adds
+ * #{f(x) < 0 and d(x) < 0} to counts[0] and #{f(x) < 0 or d(x) < 0} to
+ * counts[1] (device, 2 x uint64, accumulated); IoU = counts[0] / counts[1].
+ * Uniform points in [0,1]^3 give the volume IoU. 3-D one-channel grids. */
+TG_API tg_status tg_sdf_iou(const tg_grid *grid, const tg_shape *shape, const float *pts, int64_t N,
+                            uint64_t *counts, tg_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Differentiable ray marching (Sec. 3.3, Eq. 9 - Eq. 11).

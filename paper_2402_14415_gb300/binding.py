@@ -93,6 +93,9 @@ _SIGS = {
                     ctypes.c_float, _vp, _vp, _vp],
     "tg_tv_step": [_vp, ctypes.c_float, _vp, _vp, _vp],
     "tg_sdf_error": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
+    "tg_sdf_iou": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
+    "tg_save": [_vp, ctypes.c_char_p],
+    "tg_load": [ctypes.c_char_p, ctypes.POINTER(_vp)],
     "tg_server_create": [ctypes.c_size_t, _int, ctypes.POINTER(_vp)],
     "tg_server_destroy": [_vp],
     "tg_fit_job": [_vp, ctypes.POINTER(FitDesc), ctypes.POINTER(_i64)],
@@ -417,6 +420,25 @@ def tg_sdf_error(grid: Grid, shape: DeviceShape, pts, err_sum=None, stream=None)
     _check(load().tg_sdf_error(grid.handle, ctypes.byref(shape.struct), _ptr(pts, "pts"), pts.shape[0],
                                _ptr(err_sum, "err_sum"), _stream(stream)), "tg_sdf_error")
     return err_sum
+
+
+def tg_sdf_iou(grid: Grid, shape: DeviceShape, pts, stream=None) -> float:
+    """Volumetric IoU of {f < 0} and {d < 0} over the points (synchronises to read the counts)."""
+    counts = torch.zeros(2, device="cuda", dtype=torch.int64)
+    _check(load().tg_sdf_iou(grid.handle, ctypes.byref(shape.struct), _ptr(pts, "pts"), pts.shape[0],
+                             _ptr(counts, "counts", torch.int64), _stream(stream)), "tg_sdf_iou")
+    inter, uni = counts.tolist()
+    return inter / uni if uni else 1.0
+
+
+def tg_save(grid: Grid, path: str):
+    _check(load().tg_save(grid.handle, str(path).encode()), "tg_save")
+
+
+def tg_load(path: str) -> Grid:
+    h = _vp()
+    _check(load().tg_load(str(path).encode(), ctypes.byref(h)), "tg_load")
+    return Grid(h.value)
 
 
 def tg_render_rays(density: Grid, color: Grid, rays_o, rays_d, S: int, seed: int = 0, ray_base: int = 0,

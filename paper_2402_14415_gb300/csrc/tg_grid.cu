@@ -232,4 +232,86 @@ tg_status tg_get_coefs(const tg_grid *g, float *dst, int which, tg_stream stream
     return launch_status("tg_get_coefs: widen kernel");
 }
 
+
+/* Checkpoint format (little-endian): "TGCK", u32 version 1, i32 dim, res,
+ * order, channels, dtype, has_adam, i64 n_coefs, then the FP32 master
+ * (n_coefs floats) and, if has_adam, Adam's m and v (n_coefs floats each). */
+tg_status tg_save(const tg_grid *g, const char *path)
+{
+    if (!g || !path) return fail(TG_EINVAL, "tg_save: NULL argument");
+    const int32_t hdr[7] = {1, g->dim, g->res, g->order, g->C, (int32_t)g->dtype, g->adam_m ? 1 : 0};
+    const int64_t n = g->ncoef;
+    const size_t bytes = (size_t)n * 4;
+    float *host = (float *)malloc(bytes);
+    if (!host) return fail(TG_ENOMEM, "tg_save: host buffer");
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        free(host);
+        return fail(TG_EINVAL, "tg_save: cannot open %s for writing", path);
+    }
+    tg_status st = TG_OK;
+    bool ok = fwrite("TGCK", 1, 4, f) == 4 && fwrite(hdr, sizeof(hdr), 1, f) == 1 && fwrite(&n, 8, 1, f) == 1;
+    const float *arrays[3] = {g->master, g->adam_m, g->adam_v};
+    for (int a = 0; ok && st == TG_OK && a < (g->adam_m ? 3 : 1); ++a) {
+        st = cuda_status(cudaMemcpy(host, arrays[a], bytes, cudaMemcpyDeviceToHost), "tg_save: copy");
+        if (st == TG_OK) ok = fwrite(host, 1, bytes, f) == bytes;
+    }
+    if (fclose(f) != 0) ok = false;
+    free(host);
+    if (st != TG_OK) return st;
+    return ok ? TG_OK : fail(TG_EINVAL, "tg_save: write to %s failed", path);
+}
+
+tg_status tg_load(const char *path, tg_grid **out)
+{
+    if (!path || !out) return fail(TG_EINVAL, "tg_load: NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(TG_EINVAL, "tg_load: cannot open %s", path);
+    char magic[4];
+    int32_t hdr[7];
+    int64_t n = 0;
+    if (fread(magic, 1, 4, f) != 4 || memcmp(magic, "TGCK", 4) != 0 || fread(hdr, sizeof(hdr), 1, f) != 1 ||
+        fread(&n, 8, 1, f) != 1 || hdr[0] != 1) {
+        fclose(f);
+        return fail(TG_EINVAL, "tg_load: %s is not a TaylorGrid checkpoint (version 1)", path);
+    }
+    tg_grid *g = nullptr;
+    tg_status st = tg_create(hdr[1], hdr[2], hdr[3], hdr[4], (tg_dtype)hdr[5], 0, 0.0f, &g);
+    if (st != TG_OK) {
+        fclose(f);
+        return st;
+    }
+    if (g->ncoef != n) {
+        fclose(f);
+        tg_destroy(g);
+        return fail(TG_EINVAL, "tg_load: %s holds %lld coefficients, its shape needs %lld", path, (long long)n,
+                    (long long)g->ncoef);
+    }
+    const size_t bytes = (size_t)n * 4;
+    float *host = (float *)malloc(bytes);
+    if (!host) {
+        fclose(f);
+        tg_destroy(g);
+        return fail(TG_ENOMEM, "tg_load: host buffer");
+    }
+    const int arrays = hdr[6] ? 3 : 1;
+    if (hdr[6]) st = ensure_adam_state(g);
+    float *dst[3] = {g->master, g->adam_m, g->adam_v};
+    for (int a = 0; st == TG_OK && a < arrays; ++a) {
+        if (fread(host, 1, bytes, f) != bytes) st = fail(TG_EINVAL, "tg_load: %s is truncated", path);
+        else st = cuda_status(cudaMemcpy(dst[a], host, bytes, cudaMemcpyHostToDevice), "tg_load: copy");
+    }
+    fclose(f);
+    free(host);
+    if (st == TG_OK) st = tg_set_coefs(g, g->master, nullptr);       // the stored copy from the master
+    if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_load");
+    if (st != TG_OK) {
+        tg_destroy(g);
+        return st;
+    }
+    *out = g;
+    return TG_OK;
+}
+
 }  // extern "C"

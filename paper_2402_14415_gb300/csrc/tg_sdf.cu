@@ -169,14 +169,16 @@ sdf_loss_kernel(ShapeView s, const float4 *__restrict__ sorted, int64_t N, const
     }
 }
 
-// Sum of |f - d| over points, with f from a point-parallel gather.
+// Sum of |f - d| over points, with f from a point-parallel gather; with iou
+// also the point counts of (f < 0 and d < 0) and (f < 0 or d < 0).
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256)
 sdf_error_kernel(ShapeView s, const T *__restrict__ coefs, int res, const float *__restrict__ pts, int64_t N,
-                 float *__restrict__ err, const int *__restrict__ gate)
+                 float *__restrict__ err, const int *__restrict__ gate, unsigned long long *__restrict__ iou)
 {
     if (gate && *gate == 0) return;
     __shared__ float tmp[32];
+    unsigned inter = 0, uni = 0;
     constexpr int K = Basis<3, ORDER>::K;
     const float scale = (float)(res - 1);
     float acc = 0.f;
@@ -194,10 +196,26 @@ sdf_error_kernel(ShapeView s, const T *__restrict__ coefs, int res, const float 
             load_block<T, K>(coefs + (v0 + corner_offset<3>(I, res)) * K, th);
             f = fmaf(P.template weight<I>(), P.template value<I>(th), f);
         });
-        acc += fabsf(f - sdf_union(s, clamp01(x[0]), clamp01(x[1]), clamp01(x[2])));
+        const float d = sdf_union(s, clamp01(x[0]), clamp01(x[1]), clamp01(x[2]));
+        acc += fabsf(f - d);
+        inter += (f < 0.f && d < 0.f);
+        uni += (f < 0.f || d < 0.f);
     }
-    const float a = block_sum(acc, tmp);
-    if (threadIdx.x == 0) atomicAdd(err, a);
+    if (err) {
+        const float a = block_sum(acc, tmp);
+        if (threadIdx.x == 0) atomicAdd(err, a);
+    }
+    if (iou) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            inter += __shfl_xor_sync(0xffffffffu, inter, o);
+            uni += __shfl_xor_sync(0xffffffffu, uni, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(iou, (unsigned long long)inter);
+            atomicAdd(iou + 1, (unsigned long long)uni);
+        }
+    }
 }
 
 static unsigned blocks_for(int64_t n, int per_sm = 8)
@@ -229,10 +247,11 @@ tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, cons
 }
 
 tg_status sdf_error_impl(const tg_grid *g, const ShapeView &s, const float *pts, int64_t N, float *err_sum,
-                         const int *gate, cudaStream_t cs)
+                         const int *gate, cudaStream_t cs, unsigned long long *iou)
 {
     const unsigned nb = blocks_for(N);
-#define TG_ERR(T, O) sdf_error_kernel<T, O><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, pts, N, err_sum, gate)
+#define TG_ERR(T, O) \
+    sdf_error_kernel<T, O><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, pts, N, err_sum, gate, iou)
     if (g->dtype == TG_F32) {
         if (g->order == 0) TG_ERR(float, 0); else if (g->order == 1) TG_ERR(float, 1); else TG_ERR(float, 2);
     } else if (g->dtype == TG_BF16) {
@@ -304,6 +323,20 @@ tg_status tg_sdf_error(const tg_grid *g, const tg_shape *shape, const float *pts
     if (N == 0) return TG_OK;
     if (!pts || !err_sum) return fail(TG_EINVAL, "tg_sdf_error: NULL pts or err_sum");
     return sdf_error_impl(g, s, pts, N, err_sum, nullptr, (cudaStream_t)stream);
+}
+
+tg_status tg_sdf_iou(const tg_grid *g, const tg_shape *shape, const float *pts, int64_t N, uint64_t *counts,
+                     tg_stream stream)
+{
+    ShapeView s;
+    tg_status st = shape_view(shape, &s, "tg_sdf_iou");
+    if (st != TG_OK) return st;
+    if (!g || g->dim != 3 || g->C != 1) return fail(TG_EINVAL, "tg_sdf_iou: needs a 3-D one-channel grid");
+    if (N < 0) return fail(TG_EINVAL, "tg_sdf_iou: N < 0");
+    if (N == 0) return TG_OK;
+    if (!pts || !counts) return fail(TG_EINVAL, "tg_sdf_iou: NULL pts or counts");
+    return sdf_error_impl(g, s, pts, N, nullptr, nullptr, (cudaStream_t)stream,
+                          reinterpret_cast<unsigned long long *>(counts));
 }
 
 }  // extern "C"

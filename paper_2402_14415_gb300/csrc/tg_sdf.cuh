@@ -20,6 +20,6 @@ tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, cons
 
 // sum |f - d| over points into err_sum; skipped on the device when *gate == 0.
 tg_status sdf_error_impl(const tg_grid *g, const ShapeView &s, const float *pts, int64_t N, float *err_sum,
-                         const int *gate, cudaStream_t cs);
+                         const int *gate, cudaStream_t cs, unsigned long long *iou = nullptr);
 
 }  // namespace tg

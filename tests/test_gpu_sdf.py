@@ -147,3 +147,49 @@ def test_fit_with_the_papers_full_objective(tg):
     err = tg.tg_sdf_error(g, dshape, near).item() / near.shape[0]
     start_near = np.abs(shape.sdf(ev[ev.shape[0] // 2:])).mean()
     assert err < start_near / 4, (err, start_near)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_checkpoint_round_trip_and_resume(tg, tmp_path, dtype):
+    res, order = 20, 2
+    g = tg.tg_create(3, res, order, 1, dtype, seed=3, init_std=0.2)
+    grad = torch.randn(g.n_coefs, device="cuda")
+    tg.tg_adam_step(g, grad.clone(), lr=1e-2, step=1)              # creates Adam's moments
+    path = tmp_path / "grid.tgck"
+    tg.tg_save(g, str(path))
+    h = tg.tg_load(str(path))
+    assert (h.dim, h.res, h.order, h.channels, h.dtype) == (g.dim, g.res, g.order, g.channels, g.dtype)
+    for which in (0, 1):
+        assert torch.equal(tg.tg_get_coefs(h, which=which), tg.tg_get_coefs(g, which=which))
+    # the resumed fit takes the same next step (same moments, same gradient)
+    grad2 = torch.randn(g.n_coefs, device="cuda")
+    tg.tg_adam_step(g, grad2.clone(), lr=1e-2, step=2)
+    tg.tg_adam_step(h, grad2.clone(), lr=1e-2, step=2)
+    assert torch.equal(tg.tg_get_coefs(h, which=1), tg.tg_get_coefs(g, which=1))
+    with pytest.raises(tg.TGError):
+        tg.tg_load(str(tmp_path / "missing.tgck"))
+    (tmp_path / "bad.tgck").write_bytes(b"XXXX" + bytes(64))
+    with pytest.raises(tg.TGError):
+        tg.tg_load(str(tmp_path / "bad.tgck"))
+
+
+def test_sdf_iou_against_counts_from_the_oracle(tg):
+    """f = x - 0.3 (exact at order 1) against the box {x < 0.5}: IoU is about 0.6; the counts match the oracle's."""
+    res = 17
+    v = np.arange(res) / (res - 1)
+    X = np.broadcast_to(v[None, None, :], (res, res, res)).reshape(-1)   # vertex x coordinate, x fastest
+    coefs = np.zeros((res ** 3, 4), np.float32)
+    coefs[:, 0] = X - 0.3
+    coefs[:, 1] = 1.0
+    g = tg.tg_create(3, res, 1, 1, "f32")
+    tg.tg_set_coefs(g, to_dev(coefs.ravel()))
+    box = np.array([[0.25, 0.5, 0.5, 0.25, 0.5, 0.5]], np.float32)
+    sph = np.zeros((0, 4), np.float32)
+    shape = tg.DeviceShape(sph, box, np.array([1.0], np.float32))
+    pts = W.uniform_points(9, 200000)
+    iou = tg.tg_sdf_iou(g, shape, to_dev(pts))
+    f, _, _, _ = oracle.query(3, res, 1, 1, coefs.ravel().astype(np.float64), pts, want_grad=False)
+    d = oracle.sdf_union(sph, box, np.clip(pts, 0, 1).astype(np.float64))
+    inter, uni = np.sum((f[:, 0] < 0) & (d < 0)), np.sum((f[:, 0] < 0) | (d < 0))
+    assert abs(iou - inter / uni) <= 3 / uni, (iou, inter / uni)
+    assert abs(iou - 0.6) < 0.01
