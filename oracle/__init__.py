@@ -59,6 +59,7 @@ def lib():
             L.tgo_sdf_step.argtypes = [i32, i32, _f64p, i64, _f32p, i32, _f32p, i32, _f32p, f64, f64, _f64p, _f64p]
             L.tgo_adaptive_weight1.argtypes = [f64, f64]; L.tgo_adaptive_weight1.restype = f64
             L.tgo_tv.argtypes = [i32, i32, _f64p, f64, _f64p]; L.tgo_tv.restype = f64
+            L.tgo_resample.argtypes = [i32, i32, i32, _f64p, i32, i32, _f64p]
             L.tgo_uniform.argtypes = [u64, u64, u64]; L.tgo_uniform.restype = f64
             L.tgo_ray_box.argtypes = [_f64p, _f64p, _f64p, _f64p]; L.tgo_ray_box.restype = i32
             L.tgo_render.argtypes = [i32, i32, _f64p, i32, _f64p, i64, i32, _f32p, _f32p, u64, u64, f64,
@@ -209,4 +210,11 @@ def render_blobs(scene, rays_o, rays_d, n_samples=1024, bg=1.0):
     out = np.zeros((rays_o.shape[0], 3))
     lib().tgo_render_blobs(mu.shape[0], _p(mu, _f64p), _p(icov, _f64p), _p(amp, _f64p), _p(rgb, _f64p),
                            rays_o.shape[0], _p(rays_o, _f32p), _p(rays_d, _f32p), n_samples, bg, _p(out, _f64p))
+    return out
+
+
+def resample(res_src, order_src, C, coefs, res_dst, order_dst):
+    """The src field re-expanded as Taylor data at the vertices of a res_dst grid of order order_dst (3-D)."""
+    out = np.zeros(res_dst ** 3 * C * num_coefs(3, order_dst))
+    lib().tgo_resample(res_src, order_src, C, _p(_c(coefs, np.float64), _f64p), res_dst, order_dst, _p(out, _f64p))
     return out

@@ -195,6 +195,78 @@ TGO_API void tgo_eval_cell(int dim, int res, int order, int C, const double *coe
     }
 }
 
+/* d^2 w_i / dt_a dt_b of the multilinear weight (zero for a = b). */
+static double corner_weight_hess(int dim, int i, const double *t, int a, int b)
+{
+    if (a == b) return 0.0;
+    double w = 1.0;
+    for (int d = 0; d < dim; ++d) {
+        int bit = (i >> d) & 1;
+        if (d == a || d == b) w *= bit ? 1.0 : -1.0;
+        else w *= bit ? t[d] : 1.0 - t[d];
+    }
+    return w;
+}
+
+/* Progressive resolution (Sec. 4.1 trains coarse to fine): the field of a
+ * 3-D grid `src` (res_src, order_src, C channels) re-expanded as the Taylor
+ * data of a grid with res_dst vertices per axis and order order_dst. At every
+ * dst vertex - coordinates fl32(j / (res_dst - 1)), located in src by Eq. 2 -
+ * the dst series holds the value, the gradient and (order 2) the Hessian of
+ * f = sum_i w_i T_i (Eq. 4):
+ *   grad f = sum_i T_i grad w_i + w_i grad T_i
+ *   Hess f = sum_i T_i Hess w_i + grad w_i (grad T_i)^T + grad T_i (grad w_i)^T + w_i Hess T_i
+ * with derivatives in world units (d/dx = (res_src - 1) d/dt for w). Written
+ * in the exchange layout and the basis order of the stored series. */
+TGO_API void tgo_resample(int res_src, int order_src, int C, const double *src, int res_dst, int order_dst,
+                          double *dst)
+{
+    const int dim = 3;
+    const int Ks = tgo_num_coefs(dim, order_src), Kd = tgo_num_coefs(dim, order_dst);
+    const double h = 1.0 / (double)(res_src - 1), s = (double)(res_src - 1);
+    const int64_t nd = (int64_t)res_dst * res_dst * res_dst;
+    #pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < nd; ++v) {
+        const int64_t j[3] = {v % res_dst, (v / res_dst) % res_dst, v / ((int64_t)res_dst * res_dst)};
+        float x[3];
+        for (int a = 0; a < 3; ++a) {
+            volatile float num = (float)j[a], den = (float)(res_dst - 1);
+            x[a] = num / den;
+        }
+        int cell[3];
+        double t[3];
+        tgo_locate(dim, res_src, x, cell, t);
+        for (int ch = 0; ch < C; ++ch) {
+            double f = 0, g[3] = {0, 0, 0}, H[3][3] = {{0}};
+            for (int i = 0; i < 8; ++i) {
+                double delta[3], dT[3], f0, g0[3], H0[3][3];
+                for (int a = 0; a < 3; ++a) delta[a] = (t[a] - (double)((i >> a) & 1)) * h;
+                const double *th = src + (vertex_index(dim, res_src, cell, i) * C + ch) * Ks;
+                const double T = series_value(dim, order_src, th, delta);
+                series_gradient(dim, order_src, th, delta, dT);
+                unpack(dim, order_src, th, &f0, g0, H0);
+                const double w = corner_weight(dim, i, t);
+                double gw[3];
+                for (int a = 0; a < 3; ++a) gw[a] = corner_weight_grad(dim, i, t, a) * s;
+                f += w * T;
+                for (int a = 0; a < 3; ++a) {
+                    g[a] += gw[a] * T + w * dT[a];
+                    for (int b = 0; b < 3; ++b)
+                        H[a][b] += corner_weight_hess(dim, i, t, a, b) * s * s * T + gw[a] * dT[b] + dT[a] * gw[b] +
+                                   w * H0[a][b];
+                }
+            }
+            double *out = dst + (v * C + ch) * Kd;
+            out[0] = f;
+            if (order_dst >= 1) for (int a = 0; a < 3; ++a) out[1 + a] = g[a];
+            if (order_dst >= 2) {
+                out[4] = H[0][0]; out[5] = H[1][1]; out[6] = H[2][2];
+                out[7] = H[0][1]; out[8] = H[0][2]; out[9] = H[1][2];
+            }
+        }
+    }
+}
+
 /* Forward query of N points: values (N x C), optional world-unit spatial
  * gradients (N x C x D), optional cells (N x D) and local coordinates. */
 TGO_API void tgo_query(int dim, int res, int order, int C, const double *coefs, int64_t N,

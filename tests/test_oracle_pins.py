@@ -448,6 +448,66 @@ def test_tv_gradient_finite_differences_and_channel_separability():
         assert abs(fd - g[j]) < 1e-8 + 1e-6 * abs(fd), (j, fd, g[j])
 
 
+def fp32_vertex_coords(res):
+    """The dst vertex coordinates of the resampling rule: fl32(j / (res - 1)) in x-fastest vertex order."""
+    v = (np.arange(res, dtype=np.float32) / np.float32(res - 1)).astype(np.float64)
+    idx = np.arange(res ** 3)
+    return np.stack([v[idx % res], v[(idx // res) % res], v[idx // res ** 2]], 1)
+
+
+def taylor_at(points, order, p, grad, hess):
+    out = [np.array([p(x) for x in points])[:, None]]
+    if order >= 1:
+        out.append(np.array([grad(x) for x in points]))
+    if order >= 2:
+        Hs = np.array([hess(x) for x in points])
+        out.append(np.stack([Hs[:, 0, 0], Hs[:, 1, 1], Hs[:, 2, 2], Hs[:, 0, 1], Hs[:, 0, 2], Hs[:, 1, 2]], 1))
+    return np.concatenate(out, 1).reshape(-1)
+
+
+@pytest.mark.parametrize("res_dst", [9, 4, 7])
+def test_resample_reproduces_quadratics_and_affine_fields(res_dst):
+    p, gp, hp = quadratic(3, 90)
+    src = taylor_data_of_poly(3, 5, 2, p, gp, hp)
+    dst = oracle.resample(5, 2, 1, src, res_dst, 2)
+    np.testing.assert_allclose(dst, taylor_at(fp32_vertex_coords(res_dst), 2, p, gp, hp), atol=1e-10)
+    b = rng(91).normal(size=3)
+    aff = taylor_data_of_poly(3, 5, 1, lambda x: 0.3 + b @ x, lambda x: b, None)
+    dst = oracle.resample(5, 1, 1, aff, res_dst, 2)
+    np.testing.assert_allclose(dst, taylor_at(fp32_vertex_coords(res_dst), 2, lambda x: 0.3 + b @ x,
+                                              lambda x: b, lambda x: np.zeros((3, 3))), atol=1e-12)
+
+
+def test_resample_keeps_the_value_at_coincident_vertices():
+    src = rng(92).normal(size=5 ** 3 * 2 * 10)
+    dst = oracle.resample(5, 2, 2, src, 9, 2).reshape(9, 9, 9, 2, 10)      # [z][y][x][channel][k]
+    np.testing.assert_array_equal(dst[::2, ::2, ::2, :, 0], src.reshape(5, 5, 5, 2, 10)[..., 0])
+
+
+def test_resample_derivatives_match_finite_differences():
+    res_src, res_dst = 5, 7                 # dst coordinates j / 6 meet src faces k / 4 only at j = 0, 3, 6
+    src = rng(93).normal(size=res_src ** 3 * 10)
+    dst = oracle.resample(res_src, 2, 1, src, res_dst, 2).reshape(-1, 10)
+    X = fp32_vertex_coords(res_dst)
+    on_face = np.any(np.isin(np.round(X * 6).astype(int), [0, 3, 6]), axis=1)
+    sel = np.flatnonzero(~on_face)
+    eps = 1e-4
+    for a in range(3):
+        e = np.zeros(3); e[a] = eps
+        fp, gp, _, _ = oracle.query(3, res_src, 2, 1, src, (X[sel] + e).astype(np.float32))
+        fm, gm, _, _ = oracle.query(3, res_src, 2, 1, src, (X[sel] - e).astype(np.float32))
+        # the points are rounded to FP32 by the query: difference over the rounded step
+        step = ((X[sel] + e).astype(np.float32).astype(np.float64) - (X[sel] - e).astype(np.float32).astype(np.float64))[:, a]
+        np.testing.assert_allclose(dst[sel, 1 + a], (fp[:, 0] - fm[:, 0]) / step, rtol=1e-4, atol=1e-4)
+        Hrow = (gp[:, 0, :] - gm[:, 0, :]) / step[:, None]
+        H = np.zeros((sel.size, 3, 3))
+        H[:, 0, 0], H[:, 1, 1], H[:, 2, 2] = dst[sel, 4], dst[sel, 5], dst[sel, 6]
+        H[:, 0, 1] = H[:, 1, 0] = dst[sel, 7]
+        H[:, 0, 2] = H[:, 2, 0] = dst[sel, 8]
+        H[:, 1, 2] = H[:, 2, 1] = dst[sel, 9]
+        np.testing.assert_allclose(H[:, a, :], Hrow, rtol=1e-3, atol=1e-3 * np.abs(Hrow).max())
+
+
 # --------------------------------------------------------------------------
 # Volume rendering (Sec. 3.3, Eq. 10 / Eq. 11)
 # --------------------------------------------------------------------------
