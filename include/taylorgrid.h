@@ -117,6 +117,18 @@ TG_API tg_status tg_set_coefs(tg_grid *grid, const float *src, tg_stream stream)
  * stored copy, widened to FP32 (what queries use); which = 1: the FP32 master. */
 TG_API tg_status tg_get_coefs(const tg_grid *grid, float *dst, int which, tg_stream stream);
 
+/* Progressive resolution (Sec. 4.1 trains coarse to fine): overwrites dst's
+ * coefficients with the Taylor data of src's field (Eq. 4) at dst's vertices
+ * - the value, the world-unit gradient and, at order 2, the Hessian of the
+ * blended field, including the blend weights' derivatives - for any dst res
+ * and order (3-D grids with the same channels). A dst vertex's coordinates
+ * are fl32(j / (res_dst - 1)) and it takes the src cell of Eq. 2's rule, so a
+ * vertex on a src face takes the upper cell's one-sided derivatives. Writes
+ * dst's FP32 master and rounds its stored copy; dst's Adam state is left as
+ * is (a fresh grid has none). A src quadratic field is reproduced exactly.
+ * Errors: TG_EINVAL (NULL or 2-D grid, channel mismatch, src == dst), TG_EDEVICE. */
+TG_API tg_status tg_resample(const tg_grid *src, tg_grid *dst, tg_stream stream);
+
 /* Checkpoint / resume (synchronous; host files). tg_save writes the grid's
  * shape, its FP32 master coefficients and, if the grid has taken an Adam
  * step, Adam's two moments: format "TGCK", u32 version 1, i32 dim, res,

@@ -95,6 +95,7 @@ _SIGS = {
     "tg_sdf_error": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
     "tg_sdf_iou": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
     "tg_save": [_vp, ctypes.c_char_p],
+    "tg_resample": [_vp, _vp, _vp],
     "tg_load": [ctypes.c_char_p, ctypes.POINTER(_vp)],
     "tg_server_create": [ctypes.c_size_t, _int, ctypes.POINTER(_vp)],
     "tg_server_destroy": [_vp],
@@ -429,6 +430,11 @@ def tg_sdf_iou(grid: Grid, shape: DeviceShape, pts, stream=None) -> float:
                              _ptr(counts, "counts", torch.int64), _stream(stream)), "tg_sdf_iou")
     inter, uni = counts.tolist()
     return inter / uni if uni else 1.0
+
+
+def tg_resample(src: Grid, dst: Grid, stream=None):
+    """Re-expands src's field as dst's Taylor data (progressive resolution)."""
+    _check(load().tg_resample(src.handle, dst.handle, _stream(stream)), "tg_resample")
 
 
 def tg_save(grid: Grid, path: str):

@@ -193,3 +193,41 @@ def test_sdf_iou_against_counts_from_the_oracle(tg):
     inter, uni = np.sum((f[:, 0] < 0) & (d < 0)), np.sum((f[:, 0] < 0) | (d < 0))
     assert abs(iou - inter / uni) <= 3 / uni, (iou, inter / uni)
     assert abs(iou - 0.6) < 0.01
+
+
+@pytest.mark.parametrize("src_shape,dst_shape,dtype", [((9, 2, 1), (17, 2), "f32"), ((12, 2, 1), (7, 2), "f32"),
+                                                       ((8, 1, 3), (13, 2), "bf16"), ((6, 0, 2), (11, 1), "f32")])
+def test_resample_matches_oracle(tg, src_shape, dst_shape, dtype):
+    (rs, os_, C), (rd, od) = src_shape, dst_shape
+    src = tg.tg_create(3, rs, os_, C, dtype, seed=7, init_std=0.5)
+    dst = tg.tg_create(3, rd, od, C, dtype)
+    tg.tg_resample(src, dst)
+    got = tg.tg_get_coefs(dst, which=1).cpu().numpy().reshape(-1, (1, 4, 10)[od])
+    q = tg.tg_get_coefs(src, which=0).cpu().numpy().astype(np.float64)     # the stored copy the field uses
+    ref = oracle.resample(rs, os_, C, q, rd, od).reshape(-1, (1, 4, 10)[od])
+    # scales of the terms each entry sums: T, (res - 1) T for the gradient, (res - 1)^2 T for the Hessian
+    T = np.abs(q).max() * 3
+    s = rs - 1
+    tol = [1e-5 * T] + [1e-5 * s * T] * 3 + [1e-5 * s * s * T] * 6
+    for k in range((1, 4, 10)[od]):
+        np.testing.assert_allclose(got[:, k], ref[:, k], rtol=1e-4, atol=tol[k])
+    # the stored copy is the master rounded to the storage dtype
+    stored = tg.tg_get_coefs(dst, which=0)
+    master = tg.tg_get_coefs(dst, which=1)
+    want = master if dtype == "f32" else master.to(torch.bfloat16).float()
+    torch.testing.assert_close(stored, want, rtol=0, atol=0)
+
+
+def test_progressive_fit_continues_from_the_resampled_grid(tg):
+    """Fit at 32^3, re-expand to 64^3, keep fitting: the first fine error is close to the coarse one."""
+    shape = W.sphere_shape()
+    dshape = dev_shape(tg, shape)
+    eval_pts = to_dev(W.sdf_points(shape, seed=2, step=0, n=1 << 15))
+    coarse = tg.tg_create(3, 32, 2, 1, "f32", seed=0, init_std=1e-3)
+    rc = fit_sdf(coarse, dshape, steps=150, n_points=1 << 15, lr=1e-2, eval_pts=eval_pts)
+    fine = tg.tg_create(3, 64, 2, 1, "f32")
+    tg.tg_resample(coarse, fine)
+    e0 = tg.tg_sdf_error(fine, dshape, eval_pts).item() / eval_pts.shape[0]
+    assert e0 < 1.5 * rc.final_error, (e0, rc.final_error)
+    rf = fit_sdf(fine, dshape, steps=100, n_points=1 << 15, lr=3e-3, eval_pts=eval_pts)
+    assert rf.final_error < 1.2 * e0, (rf.final_error, e0)
