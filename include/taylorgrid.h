@@ -212,6 +212,14 @@ TG_API tg_status tg_batch_bin(tg_batch *batch, const float *pts, int64_t N, tg_s
 /* Order of the per-point arrays of the two calls below. */
 #define TG_ORDER_INPUT 0    /* the caller's original point order */
 #define TG_ORDER_BINNED 1   /* the batch's binned order (see tg_batch_order / tg_batch_points) */
+/* OR'd into the backward's flags: bitwise reproducible coefficient gradients.
+ * The brick kernels run in 8 launches, one per parity class of bricks (bricks
+ * of a class share no vertex), and each cell's points are ordered by input
+ * index before the gather, so every gradient element sums the same terms in
+ * the same order on every run - as long as every 8^3-cell brick holds at most
+ * 1024 of the batch's points (a larger brick is processed in rounds that
+ * follow the binned order). */
+#define TG_DETERMINISTIC 2
 
 /* Same outputs as tg_query / tg_query_backward for the points last binned.
  * With TG_ORDER_INPUT the per-point arrays (out, grad_x, dL_df, dL_dgradx)

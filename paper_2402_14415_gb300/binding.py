@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libtaylorgrid.so")
 
 TG_F32, TG_BF16, TG_F16 = 0, 1, 2
 TG_ORDER_INPUT, TG_ORDER_BINNED = 0, 1
+TG_DETERMINISTIC = 2
 DTYPES = {"f32": TG_F32, "fp32": TG_F32, "float32": TG_F32, "bf16": TG_BF16, "bfloat16": TG_BF16,
           "f16": TG_F16, "fp16": TG_F16, "float16": TG_F16}
 STATUS = {0: "TG_OK", 1: "TG_EINVAL", 2: "TG_ENOMEM", 3: "TG_EBUDGET", 4: "TG_ETIMEOUT", 5: "TG_EDEVICE",
@@ -294,13 +295,13 @@ def tg_query_binned(grid: Grid, batch: Batch, out=None, grad_x=None, want_grad=F
 
 
 def tg_query_backward_binned(grid: Grid, batch: Batch, dL_df, coef_grad, dL_dgradx=None, binned_order=False,
-                             stream=None):
+                             deterministic=False, stream=None):
     N = batch.n
+    flags = (TG_ORDER_BINNED if binned_order else TG_ORDER_INPUT) | (TG_DETERMINISTIC if deterministic else 0)
     _check(load().tg_query_backward_binned(grid.handle, batch.handle, _ptr(dL_df, "dL_df", numel=N * grid.channels),
                                            _ptr(dL_dgradx, "dL_dgradx", numel=N * grid.channels * grid.dim,
                                                 optional=True),
-                                           _ptr(coef_grad, "coef_grad", numel=grid.n_coefs),
-                                           TG_ORDER_BINNED if binned_order else TG_ORDER_INPUT, _stream(stream)),
+                                           _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), flags, _stream(stream)),
            "tg_query_backward_binned")
     return coef_grad
 

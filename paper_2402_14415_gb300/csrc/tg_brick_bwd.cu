@@ -17,22 +17,35 @@ constexpr int kBwdThreads = 256;
 constexpr int kPChunk = 1024;                        // points staged per round
 constexpr int kPPT = kPChunk / kBwdThreads;          // 4 staged points per thread
 
-template <int ORDER, int C, bool HAS_G>
+template <int ORDER, int C, bool HAS_G, bool DET = false>
 struct BwdLayout {
     static constexpr int NV = Basis<3, ORDER>::K * C;
     static constexpr int BXI = BoxInner<float, NV>::value;
     static constexpr int tile_floats = (kBV * kBV * BXI + 31) / 32 * 32;
     static constexpr int rec_floats = kPChunk * GatherRec<C, HAS_G>::stride;
-    static constexpr int bytes = (tile_floats + rec_floats + GatherInts::total) * 4;
+    static constexpr int key_ints = DET ? kPChunk : 0;             // input index of every staged record
+    static constexpr int bytes = (tile_floats + rec_floats + GatherInts::total + key_ints) * 4;
 };
 
-template <int ORDER, int C, bool HAS_G, bool IN_ORDER>
+// Deterministic mode: bricks run in 8 launches, one per parity class (bx, by,
+// bz mod 2) - bricks of one class share no vertex, so every gradient element
+// receives at most one reduce-add per launch, in a fixed class order - and
+// the points of every cell are ordered by input index before the gather, so
+// each vertex sums its terms in a fixed order. Bitwise reproducible whenever
+// every brick fits one round (kPChunk points): the rounds of a larger brick
+// follow the binned order, which is not fixed.
+struct DetClass {
+    int px, py, pz;       // parity of the bricks of this launch
+    int ncx, ncy;         // bricks of the class along x and y
+};
+
+template <int ORDER, int C, bool HAS_G, bool IN_ORDER, bool DET>
 __global__ void __launch_bounds__(kBwdThreads)
 brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int nby,
                  const float4 *__restrict__ sorted, const int *__restrict__ offsets, const float *__restrict__ dLdf,
-                 const float *__restrict__ dLdg)
+                 const float *__restrict__ dLdg, DetClass cls)
 {
-    using L = BwdLayout<ORDER, C, HAS_G>;
+    using L = BwdLayout<ORDER, C, HAS_G, DET>;
     using R = GatherRec<C, HAS_G>;
     constexpr int NV = L::NV;
     constexpr int BXI = L::BXI;
@@ -42,8 +55,13 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
     float *rec = tile + L::tile_floats;
     int *ints = reinterpret_cast<int *>(rec + L::rec_floats);
     int *cell_cur = ints + GatherInts::cell_cur;
+    int *rec_key = ints + GatherInts::total;                       // DET: input index per staged record
 
-    const int b = blockIdx.x;
+    int b = blockIdx.x;
+    if (DET) {
+        const int i = blockIdx.x % cls.ncx, j = (blockIdx.x / cls.ncx) % cls.ncy, k = blockIdx.x / (cls.ncx * cls.ncy);
+        b = (2 * i + cls.px) + nbx * ((2 * j + cls.py) + nby * (2 * k + cls.pz));
+    }
     const int p0 = offsets[b], p1 = offsets[b + 1];
     if (p0 == p1) return;
     const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
@@ -64,7 +82,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
         const int cnt = min(kPChunk, p1 - base);
         for (int j = tid; j < kBrickCells; j += kBwdThreads) cell_cur[j] = 0;
         __syncthreads();
-        int my_lc[kPPT];
+        int my_lc[kPPT], my_key[kPPT];
         float my_t[kPPT][3];
         float my_u[kPPT][R::fields - 3];             // upstream gradients, loaded before the cell scan
 #pragma unroll
@@ -74,6 +92,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
             if (i < cnt) {
                 const float4 q = sorted[base + i];
                 const int64_t n = IN_ORDER ? (int64_t)__float_as_int(q.w) : (int64_t)(base + i);
+                my_key[r] = __float_as_int(q.w);
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) my_u[r][ch] = __ldg(dLdf + n * C + ch);
                 if constexpr (HAS_G) {
@@ -102,8 +121,33 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
 #pragma unroll
             for (int j = 0; j < RS; j += 4)
                 *reinterpret_cast<float4 *>(rec + pos * RS + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            if (DET) rec_key[pos] = my_key[r];
         }
         __syncthreads();
+        if (DET) {   // order every cell's records by input index (cells hold a handful of points)
+            const int *off = ints + GatherInts::cell_off;
+            for (int c = tid; c < kBrickCells; c += kBwdThreads) {
+                const int lo = off[c], hi = off[c + 1];
+                for (int a = lo + 1; a < hi; ++a) {
+                    const int key = rec_key[a];
+                    float4 rv[RS / 4];
+#pragma unroll
+                    for (int j = 0; j < RS / 4; ++j) rv[j] = reinterpret_cast<const float4 *>(rec + a * RS)[j];
+                    int z = a;
+                    while (z > lo && rec_key[z - 1] > key) {
+                        rec_key[z] = rec_key[z - 1];
+#pragma unroll
+                        for (int j = 0; j < RS / 4; ++j)
+                            reinterpret_cast<float4 *>(rec + z * RS)[j] = reinterpret_cast<const float4 *>(rec + (z - 1) * RS)[j];
+                        --z;
+                    }
+                    rec_key[z] = key;
+#pragma unroll
+                    for (int j = 0; j < RS / 4; ++j) reinterpret_cast<float4 *>(rec + z * RS)[j] = rv[j];
+                }
+            }
+            __syncthreads();
+        }
         if (single) gather_round<ORDER, C, HAS_G, kBwdThreads, BXI, true>(rec, ints, tile, scale);
         else gather_round<ORDER, C, HAS_G, kBwdThreads, BXI, false>(rec, ints, tile, scale);
         __syncthreads();
@@ -120,20 +164,38 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
 
 template <int ORDER, int C, bool HAS_G, bool IN_ORDER>
 static tg_status launch_bwd(const CUtensorMap &map, const tg_grid *g, const tg_batch *bt, const float *uf,
-                            const float *ug, cudaStream_t s)
+                            const float *ug, bool det, cudaStream_t s)
 {
-    auto k = brick_bwd_kernel<ORDER, C, HAS_G, IN_ORDER>;
-    const int smem = BwdLayout<ORDER, C, HAS_G>::bytes;
+    if (!det) {
+        auto k = brick_bwd_kernel<ORDER, C, HAS_G, IN_ORDER, false>;
+        const int smem = BwdLayout<ORDER, C, HAS_G, false>::bytes;
+        tg_status st = set_smem((const void *)k, smem);
+        if (st != TG_OK) return st;
+        k<<<(unsigned)bt->nbricks, kBwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
+                                                           bt->offsets, uf, ug, DetClass{});
+        return launch_status("tg_query_backward_binned");
+    }
+    auto k = brick_bwd_kernel<ORDER, C, HAS_G, IN_ORDER, true>;
+    const int smem = BwdLayout<ORDER, C, HAS_G, true>::bytes;
     tg_status st = set_smem((const void *)k, smem);
     if (st != TG_OK) return st;
-    k<<<(unsigned)bt->nbricks, kBwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted, bt->offsets,
-                                                       uf, ug);
-    return launch_status("tg_query_backward_binned");
+    for (int cl = 0; cl < 8; ++cl) {           // the 8 parity classes, in a fixed order
+        DetClass c{cl & 1, (cl >> 1) & 1, cl >> 2, 0, 0};
+        c.ncx = (bt->nb[0] - c.px + 1) / 2;
+        c.ncy = (bt->nb[1] - c.py + 1) / 2;
+        const int ncz = (bt->nb[2] - c.pz + 1) / 2;
+        const int64_t blocks = (int64_t)c.ncx * c.ncy * ncz;
+        if (blocks == 0) continue;
+        k<<<(unsigned)blocks, kBwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted, bt->offsets, uf,
+                                                      ug, c);
+        if ((st = launch_status("tg_query_backward_binned (deterministic)")) != TG_OK) return st;
+    }
+    return TG_OK;
 }
 
 template <int DIM, int ORDER, int C>
 static tg_status binned_bwd(const tg_grid *g, const tg_batch *bt, const float *uf, const float *ug, float *grad,
-                            bool in_order, cudaStream_t s)
+                            bool in_order, bool det, cudaStream_t s)
 {
     if constexpr (DIM != 3) {
         return fail(TG_EINVAL, "binned path is 3-D only");
@@ -143,10 +205,10 @@ static tg_status binned_bwd(const tg_grid *g, const tg_batch *bt, const float *u
         tg_status st = make_brick_map(&map, grad, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->res, NV,
                                       BoxInner<float, NV>::value, kBV);
         if (st != TG_OK) return st;
-        if (ug) return in_order ? launch_bwd<ORDER, C, true, true>(map, g, bt, uf, ug, s)
-                                : launch_bwd<ORDER, C, true, false>(map, g, bt, uf, ug, s);
-        return in_order ? launch_bwd<ORDER, C, false, true>(map, g, bt, uf, nullptr, s)
-                        : launch_bwd<ORDER, C, false, false>(map, g, bt, uf, nullptr, s);
+        if (ug) return in_order ? launch_bwd<ORDER, C, true, true>(map, g, bt, uf, ug, det, s)
+                                : launch_bwd<ORDER, C, true, false>(map, g, bt, uf, ug, det, s);
+        return in_order ? launch_bwd<ORDER, C, false, true>(map, g, bt, uf, nullptr, det, s)
+                        : launch_bwd<ORDER, C, false, false>(map, g, bt, uf, nullptr, det, s);
     }
 }
 
@@ -159,14 +221,14 @@ extern "C" tg_status tg_query_backward_binned(const tg_grid *g, const tg_batch *
 {
     tg_status st = check_pair(g, bt_in, "tg_query_backward_binned");
     if (st != TG_OK) return st;
-    if (flags != TG_ORDER_INPUT && flags != TG_ORDER_BINNED)
+    if ((flags & ~(TG_ORDER_BINNED | TG_DETERMINISTIC)) != 0)
         return fail(TG_EINVAL, "tg_query_backward_binned: bad flags");
     tg_batch *bt = const_cast<tg_batch *>(bt_in);
     if (bt->n == 0) return TG_OK;
     if (!dL_df || !coef_grad) return fail(TG_EINVAL, "tg_query_backward_binned: NULL dL_df or coef_grad");
     cudaStream_t s = (cudaStream_t)stream;
-    const bool in_order = flags == TG_ORDER_INPUT;
-#define TG_BB(D, O, C) binned_bwd<D, O, C>(g, bt, dL_df, dL_dgradx, coef_grad, in_order, s)
+    const bool in_order = (flags & TG_ORDER_BINNED) == 0, det = (flags & TG_DETERMINISTIC) != 0;
+#define TG_BB(D, O, C) binned_bwd<D, O, C>(g, bt, dL_df, dL_dgradx, coef_grad, in_order, det, s)
     return TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_BB);
 #undef TG_BB
 }

@@ -137,3 +137,27 @@ def test_binned_rejects_unsupported(tg):
         tg.tg_batch_create(2, 10, 16)
     with pytest.raises(tg.TGError):
         tg.tg_batch_bin(batch, torch.rand((17, 3), device="cuda"))
+
+
+@pytest.mark.parametrize("with_g", [False, True])
+def test_deterministic_backward_is_bitwise_reproducible(tg, with_g):
+    """TG_DETERMINISTIC: the same gradient bit for bit from three independent binnings (whose binned order
+    differs from run to run), and the oracle's within tolerance."""
+    res, N = 40, 60000                        # about 480 points per brick: every brick fits one round
+    g = tg.tg_create(3, res, 2, 1, "f32", seed=2, init_std=0.5)
+    pts = W.uniform_points(51, N)
+    P = to_dev(pts)
+    r = np.random.default_rng(52)
+    up = r.normal(size=(N, 1)).astype(np.float32)
+    ug = r.normal(size=(N, 1, 3)).astype(np.float32) if with_g else None
+    grads = []
+    for _ in range(3):
+        batch = tg.tg_batch_create(3, res, N)
+        tg.tg_batch_bin(batch, P)
+        grad = torch.zeros(g.n_coefs, device="cuda")
+        tg.tg_query_backward_binned(g, batch, to_dev(up), grad, dL_dgradx=None if ug is None else to_dev(ug),
+                                    deterministic=True)
+        grads.append(grad)
+    torch.cuda.synchronize()
+    assert torch.equal(grads[0], grads[1]) and torch.equal(grads[0], grads[2])
+    check_coef_grad(grads[0].cpu().numpy(), 3, res, 2, 1, pts, up, ug)
