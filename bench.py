@@ -451,6 +451,43 @@ def bench_query_pair(steps=5, warmup=2):
             "point_parallel": round(n / (ms_pp * 1e-3) / 1e6, 1), "ms_point_parallel": round(ms_pp, 3)}
 
 
+def blob_gt(scene, rays_o, rays_d, n_samples=1024, bg=1.0, chunk=1024):
+    """Ground-truth colours of the synthetic blob scene (the Synthetic-NeRF stand-in): density
+    sum_k a_k exp(-1/2 (x - mu_k)^T P_k (x - mu_k)), colour the density-weighted mean of the blobs' rgb,
+    composited along each ray by midpoint quadrature over its [near, far] in the unit cube (bg on a miss).
+    Plain torch on the GPU, FP64, in chunks of rays; the exponent of every (sample, blob) pair is one
+    row of a matrix product of the sample's monomials (xx, yy, zz, xy, xz, yz, x, y, z, 1) with per-blob
+    coefficients. It only makes the training targets."""
+    import torch
+    mu, P, amp, rgb = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in scene)
+    Pm = torch.einsum("bac,bc->ba", P, mu)                                       # P mu
+    coef = torch.stack([P[:, 0, 0], P[:, 1, 1], P[:, 2, 2], 2 * P[:, 0, 1], 2 * P[:, 0, 2], 2 * P[:, 1, 2],
+                        -2 * Pm[:, 0], -2 * Pm[:, 1], -2 * Pm[:, 2], (mu * Pm).sum(1)], 0)   # (10, B)
+    out = []
+    for i in range(0, rays_o.shape[0], chunk):
+        o, d = rays_o[i:i + chunk].double(), rays_d[i:i + chunk].double()
+        inv = 1.0 / torch.where(d == 0, torch.full_like(d, 1e-30), d)
+        t0, t1 = (0.0 - o) * inv, (1.0 - o) * inv
+        near = torch.clamp(torch.minimum(t0, t1).amax(1), min=0.0)
+        far = torch.maximum(t0, t1).amin(1)
+        hit = far > near
+        dt = torch.where(hit, (far - near) / n_samples, torch.zeros_like(far))
+        ts = near[:, None] + (torch.arange(n_samples, device="cuda", dtype=torch.float64)[None] + 0.5) * dt[:, None]
+        x = o[:, None, :] + ts[..., None] * d[:, None, :]                        # (r, n, 3)
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        mono = torch.stack([X * X, Y * Y, Z * Z, X * Y, X * Z, Y * Z, X, Y, Z, torch.ones_like(X)], -1)
+        q = mono @ coef                                                          # (r, n, B)
+        s = amp * torch.exp(-0.5 * torch.clamp(q, min=0.0))
+        sig = s.sum(-1)
+        col = (s @ rgb) / torch.clamp(sig, min=1e-300)[..., None]
+        tau = sig * dt[:, None]
+        T = torch.exp(-(torch.cumsum(tau, 1) - tau))
+        w = T * (1 - torch.exp(-tau))
+        C = (w[..., None] * col).sum(1) + torch.exp(-tau.sum(1))[:, None] * bg
+        out.append(torch.where(hit[:, None], C, torch.full_like(C, bg)).float())
+    return torch.cat(out)
+
+
 def bench_render(steps=5, warmup=2):
     """Ray-march training step: 8192 rays x 256 samples, 160^3 density (order 2) + colour (order 1, 3 ch), BF16."""
     import torch

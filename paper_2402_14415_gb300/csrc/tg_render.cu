@@ -186,7 +186,17 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
                 dfc[a] = g[a] * Ti[k] * alpha * col[k][a] * (1.f - col[k][a]);
             }
             const int64_t sidx = r * S + i;
-            xs[3 * sidx] = xsmp[k][0]; xs[3 * sidx + 1] = xsmp[k][1]; xs[3 * sidx + 2] = xsmp[k][2];
+            if (hit) {
+                xs[3 * sidx] = xsmp[k][0]; xs[3 * sidx + 1] = xsmp[k][1]; xs[3 * sidx + 2] = xsmp[k][2];
+            } else {
+                // a missed ray's samples carry zero upstream gradient; spread them over the cube (a
+                // low-discrepancy sequence of the sample index) so the binned backward's bricks stay
+                // balanced instead of stacking them in one cell
+                const double sd = (double)sidx;
+                xs[3 * sidx] = (float)(sd * 0.7548776662466927 - floor(sd * 0.7548776662466927));
+                xs[3 * sidx + 1] = (float)(sd * 0.5698402909980532 - floor(sd * 0.5698402909980532));
+                xs[3 * sidx + 2] = (float)(sd * 0.4301597090019468 - floor(sd * 0.4301597090019468));
+            }
             ud[sidx] = hit ? dsig * sigmoid_f(fd[k]) : 0.f;      // d softplus / d f = sigmoid(f)
 #pragma unroll
             for (int a = 0; a < 3; ++a) uc[3 * sidx + a] = hit ? dfc[a] : 0.f;

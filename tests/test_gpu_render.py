@@ -91,3 +91,16 @@ def test_render_rejects_bad_arguments(tg):
         tg.tg_render_rays(dg, cg, to_dev(o), to_dev(d), S=513)
     with pytest.raises(tg.TGError):
         tg.tg_render_rays(cg, dg, to_dev(o), to_dev(d), S=16)
+
+
+def test_benchmark_ground_truth_renderer_matches_oracle(tg):
+    """bench.py renders the blob scene's training targets on the GPU; they follow the oracle's quadrature."""
+    import bench
+    scene = W.blob_scene(4)
+    o, d = W.camera_rays(100, 16, 16, cams=[3, 57])
+    o = np.concatenate([o, np.array([[2.0, 2.0, 2.0]], np.float32)])          # plus a ray that misses the cube
+    d = np.concatenate([d, np.array([[0.0, 0.0, 1.0]], np.float32)])
+    got = bench.blob_gt(scene, to_dev(o), to_dev(d), n_samples=256).cpu().numpy()
+    ref = oracle.render_blobs(scene, o, d, n_samples=256)
+    np.testing.assert_allclose(got, ref, atol=2e-4)
+    np.testing.assert_allclose(got[-1], [1, 1, 1])
