@@ -330,7 +330,7 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_extras:     # single-GPU runs only: the same on every N
         line["configs"] = {"fit_step_256_o2": bench_fit_step(), "query_only_256": bench_query_only(),
                            "query_pair_c_abi_256": bench_query_pair(),
-                           "render_160": bench_render()}
+                           "render_160": bench_render(), "render_fit_160": bench_render_fit()}
         if not args.no_serving:
             line["configs"]["serving"] = bench_serving()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -517,6 +517,52 @@ def bench_render(steps=5, warmup=2):
     return {"workload": "ray-march training step, 8192 rays x 256 samples, 160^3 BF16 density o2 + colour o1 (3 ch)",
             "train_ms_per_step": ms, "train_Msamples_per_s": R * S / (ms * 1e-3) / 1e6,
             "forward_ms": fwd, "forward_Msamples_per_s": R * S / (fwd * 1e-3) / 1e6}
+
+
+def bench_render_fit(steps=3000, res=160, R=8192, S=256, side=100, lr=(0.1, 0.03)):
+    """The ray-marching fit of the synthetic blob scene: 100 cameras on a sphere of radius 1.5 (every 10th held
+    out), targets rendered by blob_gt with 1024 midpoint samples, density (order 2) + colour (order 1, 3 ch)
+    BF16 grids, MSE photometric loss, Adam; PSNR on the held-out views."""
+    import math
+
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    scene = W.blob_scene(4)
+    cams_tr = [k for k in range(100) if k % 10 != 0]
+    cams_te = [k for k in range(100) if k % 10 == 0]
+    o_tr, d_tr = (torch.from_numpy(a).cuda() for a in W.camera_rays(100, side, side, cams=cams_tr))
+    o_te, d_te = (torch.from_numpy(a).cuda() for a in W.camera_rays(100, side, side, cams=cams_te))
+    gt_tr, gt_te = blob_gt(scene, o_tr, d_tr), blob_gt(scene, o_te, d_te)
+    dg = tg.tg_create(3, res, 2, 1, "bf16", seed=0, init_std=1e-3)
+    cg = tg.tg_create(3, res, 1, 3, "bf16", seed=1, init_std=1e-3)
+    batch = tg.tg_batch_create(3, res, R * S)
+    dgr = torch.zeros(dg.n_coefs, device="cuda")
+    cgr = torch.zeros(cg.n_coefs, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        idx = torch.randint(0, o_tr.shape[0], (R,), device="cuda", generator=gen)
+        tg.tg_render_rays(dg, cg, o_tr[idx].contiguous(), d_tr[idx].contiguous(), S=S, seed=k,
+                          target=gt_tr[idx].contiguous(), batch=batch, density_grad=dgr, color_grad=cgr, loss_sum=loss)
+        tg.tg_adam_step(dg, dgr, lr=lr[0], step=k + 1)
+        tg.tg_adam_step(cg, cgr, lr=lr[1], step=k + 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sq = 0.0
+    for i in range(0, o_te.shape[0], 1 << 16):
+        rgb = tg.tg_render_rays(dg, cg, o_te[i:i + (1 << 16)].contiguous(), d_te[i:i + (1 << 16)].contiguous(), S=S,
+                                seed=1 << 40)
+        sq += float(((rgb - gt_te[i:i + (1 << 16)]) ** 2).sum())
+    psnr = -10 * math.log10(sq / (o_te.shape[0] * 3))
+    return {"workload": f"ray-march fit of 64 Gaussian blobs: {res}^3 BF16 density o2 + colour o1, {R} rays x {S} "
+                        f"samples, {steps} steps, Adam lr {lr}; 90 training / 10 held-out cameras at {side}x{side} "
+                        "(targets by 1024-sample midpoint quadrature)",
+            "ms_per_step": ms, "held_out_psnr_db": psnr}
 
 
 def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8, deadline_s=120.0):
