@@ -658,10 +658,15 @@ def profile_once():
     # spatial-gradient variants of the two brick kernels
     tg.tg_query_binned(g, batch, out=out, grad_x=gx)
     tg.tg_query_backward_binned(g, batch, U, grad, dL_dgradx=UG)
-    # the point-parallel pair on the same unsorted points (no binning; warp-aggregated FP32 reductions)
-    tg.tg_query(g, P, out=out)
-    tg.tg_query_backward(g, P, U, grad)
+    # the point-parallel pair on the same unsorted points (no binning; warp-aggregated FP32 reductions):
+    # calls captured into a CUDA graph never bin, so the pair is captured and replayed once
+    pair = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(pair):
+        tg.tg_query(g, P, out=out)
+        tg.tg_query_backward(g, P, U, grad)
+    pair.replay()
     tg.tg_adam_step(g, grad, lr=1e-3, step=1)
+    tg.tg_tv_step(g, 2e-5, grad)              # the total variation term of the paper's fit objective
     torch.cuda.synchronize()
     print("profile pass done, timeouts:", tg.tg_batch_timeouts(batch))
 

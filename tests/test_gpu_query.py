@@ -203,3 +203,33 @@ def test_large_batches_on_two_streams_share_the_grid_batch(tg):
     torch.cuda.synchronize()
     for k, o in enumerate(outs):
         torch.testing.assert_close(o, refs[k % 2], rtol=1e-5, atol=1e-5)
+
+
+def test_large_batches_under_cuda_graph_capture(tg):
+    """Calls captured into a CUDA graph take the point-parallel kernels (binning allocates and reads back
+    sizes, so it stays out of graphs); the replayed graph matches the oracle and the binned calls."""
+    res, order, C, N = 34, 2, 1, 1 << 18
+    coefs = W.init_coefs(3, res, order, C, seed=9, std=0.5)
+    g = tg.tg_create(3, res, order, C, "f32")
+    tg.tg_set_coefs(g, to_dev(coefs))
+    pts = W.uniform_points(44, N)
+    P = to_dev(pts)
+    up = np.random.default_rng(6).normal(size=(N, C)).astype(np.float32)
+    U = to_dev(up)
+    out_binned = tg.tg_query(g, P)
+    grad_binned = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward(g, P, U, grad_binned)
+    out = torch.empty((N, C), device="cuda")
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        tg.tg_query(g, P, out=out)
+        tg.tg_query_backward(g, P, U, grad)
+    for rep in range(2):                   # the capture itself runs nothing; each replay adds one backward
+        grad.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        check_forward(out.cpu().numpy(), None, 3, res, order, C, coefs.astype(np.float64), pts)
+        check_coef_grad(grad.cpu().numpy(), 3, res, order, C, pts, up)
+        torch.testing.assert_close(out, out_binned, rtol=1e-5, atol=1e-5)
+        torch.testing.assert_close(grad, grad_binned, rtol=1e-4, atol=1e-4 * float(grad_binned.abs().max()))

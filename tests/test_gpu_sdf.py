@@ -110,7 +110,7 @@ def test_fit_low_precision_storage_tracks_fp32(tg):
 
 
 @pytest.mark.parametrize("res,order,C", [(5, 2, 1), (37, 2, 1), (40, 1, 3), (33, 0, 2), (6, 0, 1), (7, 0, 3),
-                                         (64, 2, 2)])
+                                         (64, 2, 2), (34, 1, 4), (35, 2, 3), (41, 2, 4)])
 def test_tv_step_matches_oracle(tg, res, order, C):
     """The TV term and its gradient (tiles of 32 x 8 x 32 vertices with ragged edges) against the oracle."""
     K = (1, 4, 10)[order]
