@@ -55,6 +55,7 @@ def lib():
             L.tgo_query_backward.argtypes = [i32, i32, i32, i32, i64, _f32p, _f64p, _f64p, _f64p, _f64p]
             L.tgo_query_absscale.argtypes = [i32, i32, i32, i32, _f64p, i64, _f32p, _f64p]
             L.tgo_adam.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64]
+            L.tgo_adam_lazy.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64]
             L.tgo_sdf_union.argtypes = [i32, _f32p, i32, _f32p, _f64p]; L.tgo_sdf_union.restype = f64
             L.tgo_sdf_step.argtypes = [i32, i32, _f64p, i64, _f32p, i32, _f32p, i32, _f32p, f64, f64, _f64p, _f64p]
             L.tgo_adaptive_weight1.argtypes = [f64, f64]; L.tgo_adaptive_weight1.restype = f64
@@ -141,6 +142,14 @@ def adam(p, g, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1):
     for a in (p, g, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().tgo_adam(p.size, _p(p, _f64p), _p(g, _f64p), _p(m, _f64p), _p(v, _f64p), lr, beta1, beta2, eps, step)
+
+
+def adam_lazy(p, g, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1):
+    """In-place FP64 lazy (sparse) Adam step: entries with g == 0 keep p, m and v; zeroes g."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().tgo_adam_lazy(p.size, _p(p, _f64p), _p(g, _f64p), _p(m, _f64p), _p(v, _f64p), lr, beta1, beta2, eps,
+                        step)
 
 
 def sdf_union(spheres, boxes, x):

@@ -375,6 +375,23 @@ TGO_API void tgo_adam(int64_t n, double *p, double *g, double *m, double *v,
     }
 }
 
+/* Lazy (sparse) Adam: the update above applied only to the entries whose
+ * gradient is nonzero; the others keep their parameter and both moments (no
+ * decay). The bias corrections use the global step. */
+TGO_API void tgo_adam_lazy(int64_t n, double *p, double *g, double *m, double *v,
+                           double lr, double beta1, double beta2, double eps, int64_t step)
+{
+    double bc1 = 1.0 - pow(beta1, (double)step);
+    double bc2 = 1.0 - pow(beta2, (double)step);
+    for (int64_t j = 0; j < n; ++j) {
+        if (g[j] == 0.0) continue;
+        m[j] = beta1 * m[j] + (1.0 - beta1) * g[j];
+        v[j] = beta2 * v[j] + (1.0 - beta2) * g[j] * g[j];
+        p[j] -= lr * (m[j] / bc1) / (sqrt(v[j] / bc2) + eps);
+        g[j] = 0.0;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* SDF targets (Sec. 3.2, Eq. 5): analytic signed distances                  */
 /* ------------------------------------------------------------------------ */

@@ -296,6 +296,42 @@ def test_adam_matches_torch():
         opt.step()
         np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
 
+def test_lazy_adam_matches_torch_sparse_adam():
+    """Lazy Adam against torch.optim.SparseAdam (float64) fed the nonzero entries as a sparse gradient; entries
+    with a zero gradient keep p, m and v; with no zero entries it is plain Adam. SparseAdam adds eps to sqrt(v)
+    before the bias correction, Adam (and the oracle) to sqrt(v_hat): the two agree to rounding at eps = 1e-30
+    (SparseAdam refuses 0), and the dense case pins the eps placement to the Adam oracle, itself pinned to
+    torch.optim.Adam."""
+    r = rng(61)
+    n = 1000
+    p0 = r.normal(size=n)
+    p = p0.copy(); m = np.zeros(n); v = np.zeros(n)
+    tp = torch.tensor(p0, requires_grad=True)
+    opt = torch.optim.SparseAdam([tp], lr=3e-3, betas=(0.9, 0.999), eps=1e-30)
+    for step in range(1, 7):
+        g = r.normal(size=n) * (r.random(n) < 0.4)          # about 60 % untouched entries per step
+        before = (p.copy(), m.copy(), v.copy())
+        gg = g.copy()
+        oracle.adam_lazy(p, gg, m, v, 3e-3, 0.9, 0.999, 1e-30, step)
+        assert not gg.any()
+        idx = np.nonzero(g)[0]
+        tp.grad = torch.sparse_coo_tensor(torch.tensor(idx)[None], torch.tensor(g[idx]), (n,),
+                                          check_invariants=True)
+        opt.step()
+        np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+        z = g == 0
+        for a, b in zip((p, m, v), before):
+            assert np.array_equal(a[z], b[z])
+    # dense gradient: the lazy rule is plain Adam
+    q = p0.copy(); mq = np.zeros(n); vq = np.zeros(n)
+    p = p0.copy(); m = np.zeros(n); v = np.zeros(n)
+    for step in range(1, 4):
+        g = r.normal(size=n)
+        g[g == 0] = 1.0
+        oracle.adam(q, g.copy(), mq, vq, 1e-2, 0.9, 0.999, 1e-8, step)
+        oracle.adam_lazy(p, g.copy(), m, v, 1e-2, 0.9, 0.999, 1e-8, step)
+    assert np.array_equal(p, q) and np.array_equal(m, mq) and np.array_equal(v, vq)
+
 
 # --------------------------------------------------------------------------
 # SDF targets and the SDF step (Sec. 3.2)
