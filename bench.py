@@ -387,6 +387,17 @@ def bench_fit_step(steps=10, warmup=3):
                 k[0] += 1
             ms = _time_ms(step_full, steps, warmup)
             out["f32_paper_objective"] = {"ms_per_step": ms, "Mpts_per_s": n / (ms * 1e-3) / 1e6}
+            def step_lazy():   # the same step with lazy Adam (untouched coefficients keep parameter and moments)
+                tg.tg_sdf_step(g, batch, dsh, grad, loss, n=n, seed=1, step=k[0], lambda_eik=0.1)
+                tg.tg_adam_step_lazy(g, grad, lr=5e-3, step=k[0] + 1)
+                k[0] += 1
+            ms = _time_ms(step_lazy, steps, warmup)
+            out["f32_lazy_adam"] = {"ms_per_step": ms, "Mpts_per_s": n / (ms * 1e-3) / 1e6}
+            ms_adam = _time_ms(lambda: tg.tg_adam_step(g, grad, lr=5e-3, step=1), steps, warmup)
+            adam_bytes = 32.0 * g.n_coefs          # read p, g, m, v; write p, m, v and the zeroed g
+            out["adam_kernel"] = {"ms": ms_adam, "algorithmic_GB": adam_bytes / 1e9,
+                                  "achieved_GBps": adam_bytes / (ms_adam * 1e-3) / 1e9,
+                                  "frac_of_measured_hbm_peak": adam_bytes / (ms_adam * 1e-3) / 1e9 / peaks()[0]}
             ms_tv = _time_ms(lambda: tg.tg_tv_step(g, 2e-5, grad), steps, warmup)
             tv_bytes = 12.0 * g.n_coefs            # read theta, read + write the gradient
             out["tv_kernel"] = {"ms": ms_tv, "algorithmic_GB": tv_bytes / 1e9,

@@ -300,6 +300,18 @@ typedef struct {
  * Errors: TG_EINVAL (NULL, step < 1), TG_ENOMEM, TG_EDEVICE. */
 TG_API tg_status tg_adam_step(tg_grid *grid, float *coef_grad, const tg_adam *params, tg_stream stream);
 
+/* Lazy (sparse) Adam: as tg_adam_step, but a coefficient whose gradient is
+ * exactly 0 this step keeps its parameter and both moments (its moments do
+ * not decay); the others take the update above with the bias corrections of
+ * the global step. This changes the optimiser: a coefficient that no point
+ * touches stops moving instead of coasting on its first moment. It is the
+ * rule of torch.optim.SparseAdam except for the placement of eps, which here
+ * is added to sqrt(v_hat) as in tg_adam_step. A group of four coefficients
+ * with zero gradients costs only its 16-byte gradient read, so steps that
+ * touch a small part of the grid move far fewer bytes. Zeroes coef_grad.
+ * Errors as tg_adam_step. */
+TG_API tg_status tg_adam_step_lazy(tg_grid *grid, float *coef_grad, const tg_adam *params, tg_stream stream);
+
 /* ---------------------------------------------------------------------------
  * SDF fitting (Sec. 3.2). The target S is the zero level set of an analytic
  * signed distance (Eq. 5): a union of spheres and axis-aligned boxes.

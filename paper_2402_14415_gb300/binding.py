@@ -88,6 +88,7 @@ _SIGS = {
     "tg_batch_scatter": [_vp, _vp, _int, _vp, _vp],
     "tg_query_noalloc": [_vp, _vp, _i64, _vp, _vp, _vp],
     "tg_adam_step": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
+    "tg_adam_step_lazy": [_vp, _vp, ctypes.POINTER(AdamParams), _vp],
     "tg_sdf_eval_target": [ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
     "tg_sample_sdf_points": [ctypes.POINTER(ShapeStruct), ctypes.c_uint64, _i64, _i64, ctypes.c_float, _vp, _vp],
     "tg_sdf_step": [_vp, _vp, ctypes.POINTER(ShapeStruct), _vp, _i64, ctypes.c_uint64, _i64, ctypes.c_float,
@@ -368,6 +369,12 @@ def tg_adam_step(grid: Grid, coef_grad, lr: float, step: int, beta1=0.9, beta2=0
     prm = AdamParams(lr, beta1, beta2, eps, step)
     _check(load().tg_adam_step(grid.handle, _ptr(coef_grad, "coef_grad", numel=grid.n_coefs), ctypes.byref(prm),
                                _stream(stream)), "tg_adam_step")
+
+
+def tg_adam_step_lazy(grid: Grid, coef_grad, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    prm = AdamParams(lr, beta1, beta2, eps, step)
+    _check(load().tg_adam_step_lazy(grid.handle, _ptr(coef_grad, "coef_grad", numel=grid.n_coefs),
+                                    ctypes.byref(prm), _stream(stream)), "tg_adam_step_lazy")
 
 
 class DeviceShape:

@@ -44,8 +44,15 @@ __device__ __forceinline__ void store4<__half>(__half *dst, int64_t j, float a, 
     *reinterpret_cast<uint2 *>(dst + j) = u;
 }
 
+// LAZY: entries whose gradient is 0 keep parameter and moments; a group of
+// four zero gradients costs only its 16-byte gradient read.
+__device__ __forceinline__ void adam_lazy_one(float &p, float g, float &m, float &v, const AdamCoef &a)
+{
+    if (g != 0.0f) adam_one(p, g, m, v, a);
+}
+
 // Vectorised body over n4 = n / 4 float4 groups, scalar tail handled by block 0.
-template <typename T>
+template <typename T, bool LAZY = false>
 __global__ void __launch_bounds__(256)
 adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
             T *__restrict__ shadow, int64_t n, AdamCoef a, const int64_t *__restrict__ step_dev, float lr)
@@ -62,11 +69,20 @@ adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
     float4 *m4 = reinterpret_cast<float4 *>(m);
     float4 *v4 = reinterpret_cast<float4 *>(v);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += stride) {
-        float4 pp = p4[j], gg = __ldcs(g4 + j), mm = m4[j], vv = v4[j];
-        adam_one(pp.x, gg.x, mm.x, vv.x, a);
-        adam_one(pp.y, gg.y, mm.y, vv.y, a);
-        adam_one(pp.z, gg.z, mm.z, vv.z, a);
-        adam_one(pp.w, gg.w, mm.w, vv.w, a);
+        const float4 gg = __ldcs(g4 + j);
+        if (LAZY && gg.x == 0.f && gg.y == 0.f && gg.z == 0.f && gg.w == 0.f) continue;
+        float4 pp = p4[j], mm = m4[j], vv = v4[j];
+        if (LAZY) {
+            adam_lazy_one(pp.x, gg.x, mm.x, vv.x, a);
+            adam_lazy_one(pp.y, gg.y, mm.y, vv.y, a);
+            adam_lazy_one(pp.z, gg.z, mm.z, vv.z, a);
+            adam_lazy_one(pp.w, gg.w, mm.w, vv.w, a);
+        } else {
+            adam_one(pp.x, gg.x, mm.x, vv.x, a);
+            adam_one(pp.y, gg.y, mm.y, vv.y, a);
+            adam_one(pp.z, gg.z, mm.z, vv.z, a);
+            adam_one(pp.w, gg.w, mm.w, vv.w, a);
+        }
         p4[j] = pp;
         m4[j] = mm;
         v4[j] = vv;
@@ -75,6 +91,7 @@ adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
     }
     if (blockIdx.x == 0) {
         for (int64_t j = 4 * n4 + threadIdx.x; j < n; j += blockDim.x) {
+            if (LAZY && g[j] == 0.f) continue;
             float pp = p[j], mm = m[j], vv = v[j];
             adam_one(pp, g[j], mm, vv, a);
             p[j] = pp; m[j] = mm; v[j] = vv; g[j] = 0.0f;
@@ -106,7 +123,7 @@ tg_status ensure_adam_state(tg_grid *g)
 
 // Adam over all coefficients; with step_dev the 0-based step index is read on
 // the device (for replayable CUDA graphs) and prm->step is ignored.
-tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t *step_dev, cudaStream_t s)
+tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t *step_dev, cudaStream_t s, bool lazy)
 {
     tg_status st = ensure_adam_state(g);
     if (st != TG_OK) return st;
@@ -124,26 +141,41 @@ tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t
     int64_t need = (n4 + 255) / 256;
     int64_t cap = (int64_t)num_sms() * per_sm;
     unsigned nb = (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
-    if (g->dtype == TG_F32)
-        adam_kernel<float><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, nullptr, g->ncoef, a, step_dev,
-                                              prm->lr);
-    else if (g->dtype == TG_BF16)
-        adam_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v,
-                                                      (__nv_bfloat16 *)g->store, g->ncoef, a, step_dev, prm->lr);
-    else
-        adam_kernel<__half><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, (__half *)g->store, g->ncoef, a,
-                                               step_dev, prm->lr);
-    return launch_status("tg_adam_step");
+#define TG_ADAM(T, L, SH) adam_kernel<T, L><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, SH, g->ncoef, \
+                                                              a, step_dev, prm->lr)
+    if (g->dtype == TG_F32) {
+        if (lazy) TG_ADAM(float, true, nullptr);
+        else TG_ADAM(float, false, nullptr);
+    } else if (g->dtype == TG_BF16) {
+        if (lazy) TG_ADAM(__nv_bfloat16, true, (__nv_bfloat16 *)g->store);
+        else TG_ADAM(__nv_bfloat16, false, (__nv_bfloat16 *)g->store);
+    } else {
+        if (lazy) TG_ADAM(__half, true, (__half *)g->store);
+        else TG_ADAM(__half, false, (__half *)g->store);
+    }
+#undef TG_ADAM
+    return launch_status(lazy ? "tg_adam_step_lazy" : "tg_adam_step");
 }
 
 }  // namespace tg
 
+static tg_status adam_entry(tg_grid *g, float *grad, const tg_adam *prm, tg_stream stream, bool lazy)
+{
+    const char *name = lazy ? "tg_adam_step_lazy" : "tg_adam_step";
+    if (!g || !grad || !prm) return fail(TG_EINVAL, "%s: NULL argument", name);
+    if (prm->step < 1) return fail(TG_EINVAL, "%s: step must be >= 1", name);
+    if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
+        return fail(TG_EINVAL, "%s: betas must lie in [0,1) and eps >= 0", name);
+    if (((uintptr_t)grad & 15) != 0) return fail(TG_EINVAL, "%s: coef_grad must be 16-byte aligned", name);
+    return adam_launch(g, grad, prm, nullptr, (cudaStream_t)stream, lazy);
+}
+
 extern "C" tg_status tg_adam_step(tg_grid *g, float *grad, const tg_adam *prm, tg_stream stream)
 {
-    if (!g || !grad || !prm) return fail(TG_EINVAL, "tg_adam_step: NULL argument");
-    if (prm->step < 1) return fail(TG_EINVAL, "tg_adam_step: step must be >= 1");
-    if (!(prm->beta1 >= 0.f && prm->beta1 < 1.f && prm->beta2 >= 0.f && prm->beta2 < 1.f && prm->eps >= 0.f))
-        return fail(TG_EINVAL, "tg_adam_step: betas must lie in [0,1) and eps >= 0");
-    if (((uintptr_t)grad & 15) != 0) return fail(TG_EINVAL, "tg_adam_step: coef_grad must be 16-byte aligned");
-    return adam_launch(g, grad, prm, nullptr, (cudaStream_t)stream);
+    return adam_entry(g, grad, prm, stream, false);
+}
+
+extern "C" tg_status tg_adam_step_lazy(tg_grid *g, float *grad, const tg_adam *prm, tg_stream stream)
+{
+    return adam_entry(g, grad, prm, stream, true);
 }

@@ -45,8 +45,10 @@ tg_status query_backward_point_parallel(const tg_grid *g, const float *pts, int6
                                         const float *dL_dgradx, float *coef_grad, cudaStream_t s);
 
 // Adam over all coefficients (tg_adam.cu); with step_dev != nullptr the
-// 0-based step index is read on the device and prm->step is ignored.
-tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t *step_dev, cudaStream_t s);
+// 0-based step index is read on the device and prm->step is ignored; lazy
+// skips the entries whose gradient is 0 (tg_adam_step_lazy).
+tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t *step_dev, cudaStream_t s,
+                      bool lazy = false);
 tg_status ensure_adam_state(tg_grid *g);
 
 inline int num_coefs(int dim, int order)

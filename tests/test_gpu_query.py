@@ -155,6 +155,36 @@ def test_adam_parity(tg, dtype):
     assert np.array_equal(stored, want.float().numpy())
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_lazy_adam_parity(tg, dtype):
+    """tg_adam_step_lazy against the oracle's lazy Adam on gradients that leave whole vertices (groups of 4
+    coefficients and more) and single coefficients at 0; untouched entries keep their bits."""
+    dim, res, order, C = 3, 7, 2, 1                    # 3430 coefficients: a scalar tail after the float4 groups
+    g, coefs = make_grid(tg, dim, res, order, C, dtype=dtype)
+    n = g.n_coefs
+    p = coefs.astype(np.float64).copy(); m = np.zeros(n); v = np.zeros(n)
+    r = np.random.default_rng(12)
+    grad = torch.zeros(n, device="cuda")
+    for step in range(1, 6):
+        gnp = r.normal(size=n).astype(np.float32)
+        gnp *= np.repeat(r.random(n // 10 + 1) < 0.5, 10)[:n]          # whole vertices untouched
+        gnp[r.random(n) < 0.05] = 0.0                                   # and single coefficients
+        before = tg.tg_get_coefs(g, which=1).cpu().numpy()
+        grad.copy_(to_dev(gnp))
+        tg.tg_adam_step_lazy(g, grad, lr=1e-2, step=step)
+        oracle.adam_lazy(p, gnp.astype(np.float64), m, v, 1e-2, 0.9, 0.999, 1e-8, step)
+        torch.cuda.synchronize()
+        assert not grad.any()
+        got = tg.tg_get_coefs(g, which=1).cpu().numpy()
+        z = gnp == 0
+        assert np.array_equal(got[z], before[z])
+        np.testing.assert_allclose(got, p, rtol=0, atol=2e-6 * step * 1e-2 * 10 + 1e-6 * np.abs(p).max())
+    stored = tg.tg_get_coefs(g, which=0).cpu().numpy()
+    master = tg.tg_get_coefs(g, which=1).cpu()
+    want = master.to(torch.bfloat16 if dtype == "bf16" else torch.float32)
+    assert np.array_equal(stored, want.float().numpy())
+
+
 def test_init_matches_generator(tg):
     g = tg.tg_create(3, 6, 2, 1, "f32", seed=42, init_std=0.01)
     got = tg.tg_get_coefs(g, which=1).cpu().numpy()
