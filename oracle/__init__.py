@@ -62,6 +62,8 @@ def lib():
             L.tgo_tv.argtypes = [i32, i32, _f64p, f64, _f64p]; L.tgo_tv.restype = f64
             L.tgo_resample.argtypes = [i32, i32, i32, _f64p, i32, i32, _f64p]
             L.tgo_uniform.argtypes = [u64, u64, u64]; L.tgo_uniform.restype = f64
+            L.tgo_marching_tets.argtypes = [i32, _f64p, f64, _f64p, i64]; L.tgo_marching_tets.restype = i64
+            L.tgo_sample_mesh.argtypes = [i64, _f32p, i64, u64, u64, _f64p]
             L.tgo_ray_box.argtypes = [_f64p, _f64p, _f64p, _f64p]; L.tgo_ray_box.restype = i32
             L.tgo_render.argtypes = [i32, i32, _f64p, i32, _f64p, i64, i32, _f32p, _f32p, u64, u64, f64,
                                      _f64p, _f32p, _f64p, _f64p, _f64p]
@@ -187,6 +189,46 @@ def tv(res, nv, coefs, lam=1.0, want_grad=True):
 
 def uniform(seed, stream, idx) -> float:
     return lib().tgo_uniform(seed, stream, idx)
+
+
+def lattice_values(res, order, C, coefs, M, channel=0):
+    """The field (channel `channel`) at the M^3 lattice x = (i, j, k) / (M - 1), i fastest (FP64)."""
+    a = np.arange(M, dtype=np.float64) / (M - 1)
+    z, y, x = np.meshgrid(a, a, a, indexing="ij")
+    pts = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1).astype(np.float32)
+    f, _, _, _ = query(3, res, order, C, coefs, pts, want_grad=False)
+    return f.reshape(-1, C)[:, channel].copy()
+
+
+def marching_tets(M, vals, iso=0.0):
+    """Triangles (T, 3, 3) of the iso surface of the M^3 lattice values (i fastest), in cube order."""
+    vals = np.ascontiguousarray(vals, np.float64).reshape(-1)
+    assert vals.size == M ** 3
+    n = lib().tgo_marching_tets(M, _p(vals, _f64p), iso, None, 0)
+    tris = np.zeros((max(n, 1), 9))
+    lib().tgo_marching_tets(M, _p(vals, _f64p), iso, _p(tris, _f64p), n)
+    return tris[:n].reshape(n, 3, 3)
+
+
+MESH_STREAM = 0x4D455348          # generator stream of the mesh sampler
+
+
+def sample_mesh(tris, n, seed):
+    """n area-weighted points on the triangles (T, 3, 3) given in FP32."""
+    t = np.ascontiguousarray(tris, np.float32).reshape(-1)
+    out = np.zeros((n, 3))
+    lib().tgo_sample_mesh(t.size // 9, _p(t, _f32p), n, seed, MESH_STREAM, _p(out, _f64p))
+    return out
+
+
+def chamfer(A, B):
+    """(sum_a min_b |a - b|^2, sum_b min_a |a - b|^2) in FP64; the nearest neighbours come from a k-d tree
+    (scipy.spatial.cKDTree, exact)."""
+    from scipy.spatial import cKDTree
+    A = np.asarray(A, np.float64).reshape(-1, 3); B = np.asarray(B, np.float64).reshape(-1, 3)
+    da, _ = cKDTree(B).query(A)
+    db, _ = cKDTree(A).query(B)
+    return float((da * da).sum()), float((db * db).sum())
 
 
 def ray_box(o, d):

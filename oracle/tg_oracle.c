@@ -529,6 +529,162 @@ TGO_API double tgo_uniform(uint64_t seed, uint64_t stream, uint64_t idx)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Mesh extraction: marching tetrahedra over a lattice of field values       */
+/* ------------------------------------------------------------------------ */
+/* Every lattice cube (corner q at offset (q & 1, q >> 1 & 1, q >> 2)) is cut
+ * into the six tetrahedra that share its main diagonal 0 - 7, one per order
+ * in which a monotone path from corner 0 to corner 7 visits the axes, so
+ * neighbouring cubes cut their common faces alike and the surface closes. */
+static const int kTets[6][4] = {{0, 1, 3, 7}, {0, 1, 5, 7}, {0, 2, 3, 7}, {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 6, 7}};
+
+/* The iso crossing on the lattice edge a - b, taken from its lower-indexed end
+ * so that every tetrahedron sharing the edge gets the same point. */
+static void mt_cross(int M, const int *a, const int *b, double fa, double fb, double iso, double *p)
+{
+    const int64_t ia = a[0] + (int64_t)M * (a[1] + (int64_t)M * a[2]);
+    const int64_t ib = b[0] + (int64_t)M * (b[1] + (int64_t)M * b[2]);
+    if (ia > ib) {
+        const int *tc = a; a = b; b = tc;
+        double tf = fa; fa = fb; fb = tf;
+    }
+    const double t = (iso - fa) / (fb - fa);
+    for (int d = 0; d < 3; ++d) p[d] = (a[d] + t * (b[d] - a[d])) / (double)(M - 1);
+}
+
+/* Writes triangle (a, b, c), or (a, c, b) if its normal points against dir. */
+static void mt_emit(double *tris, int64_t *n, int64_t max, const double *a, const double *b, const double *c,
+                    const double *dir)
+{
+    double u[3], v[3];
+    for (int d = 0; d < 3; ++d) { u[d] = b[d] - a[d]; v[d] = c[d] - a[d]; }
+    const double nx = u[1] * v[2] - u[2] * v[1], ny = u[2] * v[0] - u[0] * v[2], nz = u[0] * v[1] - u[1] * v[0];
+    const int flip = nx * dir[0] + ny * dir[1] + nz * dir[2] < 0.0;
+    if (*n < max) {
+        double *o = tris + 9 * *n;
+        for (int d = 0; d < 3; ++d) {
+            o[d] = a[d];
+            o[3 + d] = flip ? c[d] : b[d];
+            o[6 + d] = flip ? b[d] : c[d];
+        }
+    }
+    ++*n;
+}
+
+/* Marching tetrahedra over the M^3 lattice vals[i + M (j + M k)] at
+ * x = (i, j, k) / (M - 1): a lattice point is inside where its value, rounded
+ * to FP32, is below iso (rounded likewise). Triangles are oriented toward
+ * increasing values and written (9 doubles each, up to max_tris) in cube order
+ * (k, then j, then i), the six tetrahedra in the order of kTets, a quad as the
+ * two triangles (q0 q1 q2) (q0 q2 q3). Returns the number of triangles. */
+TGO_API int64_t tgo_marching_tets(int M, const double *vals, double iso, double *tris, int64_t max_tris)
+{
+    int64_t n = 0;
+    const float iso32 = (float)iso;
+    for (int k = 0; k + 1 < M; ++k)
+        for (int j = 0; j + 1 < M; ++j)
+            for (int i = 0; i + 1 < M; ++i) {
+                int cc[8][3];
+                double f[8];
+                for (int q = 0; q < 8; ++q) {
+                    cc[q][0] = i + (q & 1); cc[q][1] = j + ((q >> 1) & 1); cc[q][2] = k + (q >> 2);
+                    f[q] = (double)(float)vals[cc[q][0] + (int64_t)M * (cc[q][1] + (int64_t)M * cc[q][2])];
+                }
+                for (int tt = 0; tt < 6; ++tt) {
+                    const int *tv = kTets[tt];
+                    int in[4], nin = 0;
+                    for (int a = 0; a < 4; ++a) { in[a] = (float)f[tv[a]] < iso32; nin += in[a]; }
+                    if (nin == 0 || nin == 4) continue;
+                    double pos[4][3];
+                    for (int a = 0; a < 4; ++a)
+                        for (int d = 0; d < 3; ++d) pos[a][d] = cc[tv[a]][d] / (double)(M - 1);
+                    if (nin == 1 || nin == 3) {
+                        int o = 0;                        /* the vertex on its own side */
+                        for (int a = 0; a < 4; ++a)
+                            if (in[a] == (nin == 1)) o = a;
+                        double e[3][3], cen[3] = {0, 0, 0}, dir[3];
+                        int m = 0;
+                        for (int a = 0; a < 4; ++a) {
+                            if (a == o) continue;
+                            mt_cross(M, cc[tv[o]], cc[tv[a]], f[tv[o]], f[tv[a]], iso32, e[m]);
+                            for (int d = 0; d < 3; ++d) cen[d] += e[m][d] / 3.0;
+                            ++m;
+                        }
+                        for (int d = 0; d < 3; ++d) dir[d] = nin == 1 ? cen[d] - pos[o][d] : pos[o][d] - cen[d];
+                        mt_emit(tris, &n, max_tris, e[0], e[1], e[2], dir);
+                    } else {
+                        int ii[2], oo[2], a_i = 0, a_o = 0;
+                        for (int a = 0; a < 4; ++a) {
+                            if (in[a]) ii[a_i++] = a;
+                            else oo[a_o++] = a;
+                        }
+                        double q[4][3], dir[3];
+                        const int pa[4][2] = {{ii[0], oo[0]}, {ii[0], oo[1]}, {ii[1], oo[1]}, {ii[1], oo[0]}};
+                        for (int r = 0; r < 4; ++r)
+                            mt_cross(M, cc[tv[pa[r][0]]], cc[tv[pa[r][1]]], f[tv[pa[r][0]]], f[tv[pa[r][1]]], iso32, q[r]);
+                        for (int d = 0; d < 3; ++d)
+                            dir[d] = 0.5 * (pos[oo[0]][d] + pos[oo[1]][d]) - 0.5 * (pos[ii[0]][d] + pos[ii[1]][d]);
+                        /* both halves take the orientation of (q0 q1 q2); reversing it swaps q1 and q3 */
+                        double u[3], v[3];
+                        for (int d = 0; d < 3; ++d) { u[d] = q[1][d] - q[0][d]; v[d] = q[2][d] - q[0][d]; }
+                        const double nx = u[1] * v[2] - u[2] * v[1], ny = u[2] * v[0] - u[0] * v[2],
+                                     nz = u[0] * v[1] - u[1] * v[0];
+                        if (nx * dir[0] + ny * dir[1] + nz * dir[2] < 0.0) {
+                            double t3[3];
+                            for (int d = 0; d < 3; ++d) { t3[d] = q[1][d]; q[1][d] = q[3][d]; q[3][d] = t3[d]; }
+                        }
+                        if (n < max_tris) {
+                            double *o = tris + 9 * n;
+                            for (int d = 0; d < 3; ++d) { o[d] = q[0][d]; o[3 + d] = q[1][d]; o[6 + d] = q[2][d]; }
+                        }
+                        ++n;
+                        if (n < max_tris) {
+                            double *o = tris + 9 * n;
+                            for (int d = 0; d < 3; ++d) { o[d] = q[0][d]; o[3 + d] = q[2][d]; o[6 + d] = q[3][d]; }
+                        }
+                        ++n;
+                    }
+                }
+            }
+    return n;
+}
+
+/* Area-weighted points on a triangle soup (T x 9 floats): sample s takes
+ * u = U(seed, stream, 3 s) times the total area and the first triangle whose
+ * inclusive running area (summed in triangle order, FP64) exceeds it, then
+ * r1 = U(.., 3 s + 1), r2 = U(.., 3 s + 2) and the point
+ * (1 - sqrt r1) v0 + sqrt r1 (1 - r2) v1 + sqrt r1 r2 v2. */
+TGO_API void tgo_sample_mesh(int64_t T, const float *tris, int64_t N, uint64_t seed, uint64_t stream, double *out)
+{
+    double *cum = (double *)malloc((size_t)(T > 0 ? T : 1) * sizeof(double));
+    double run = 0.0;
+    for (int64_t j = 0; j < T; ++j) {
+        const float *t = tris + 9 * j;
+        double u[3], v[3];
+        for (int d = 0; d < 3; ++d) { u[d] = (double)t[3 + d] - t[d]; v[d] = (double)t[6 + d] - t[d]; }
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+        run += 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+        cum[j] = run;
+    }
+    const uint64_t key = mix64(mix64(seed) + stream);
+    for (int64_t s = 0; s < N; ++s) {
+        const double u0 = (double)(mix64(key + 3 * (uint64_t)s) >> 40) * (1.0 / 16777216.0);
+        const double r1 = (double)(mix64(key + 3 * (uint64_t)s + 1) >> 40) * (1.0 / 16777216.0);
+        const double r2 = (double)(mix64(key + 3 * (uint64_t)s + 2) >> 40) * (1.0 / 16777216.0);
+        const double target = u0 * run;
+        int64_t lo = 0, hi = T - 1;              /* first j with cum[j] > target */
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (cum[mid] > target) hi = mid;
+            else lo = mid + 1;
+        }
+        const float *t = tris + 9 * lo;
+        const double sr = sqrt(r1), a = 1.0 - sr, b = sr * (1.0 - r2), c = sr * r2;
+        for (int d = 0; d < 3; ++d) out[3 * s + d] = a * t[d] + b * t[3 + d] + c * t[6 + d];
+    }
+    free(cum);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Volume rendering (Sec. 3.3, Eq. 9 - Eq. 11)                                */
 /* ------------------------------------------------------------------------ */
 static double softplus(double x) { return x > 30.0 ? x : log1p(exp(x)); }

@@ -622,3 +622,95 @@ def test_blob_scene_renderer_limits():
     np.testing.assert_allclose(c[1], [1, 1, 1])
     c0 = oracle.render_blobs((mu, icov, np.array([0.0]), rgb), o, d, n_samples=64, bg=0.25)
     np.testing.assert_allclose(c0, 0.25)
+
+
+# --------------------------------------------------------------------------
+# Mesh extraction (marching tetrahedra), mesh sampling and the Chamfer distance
+# --------------------------------------------------------------------------
+def _lattice(M, fn):
+    a = np.arange(M, dtype=np.float64) / (M - 1)
+    z, y, x = np.meshgrid(a, a, a, indexing="ij")
+    return fn(x, y, z).ravel()
+
+
+@pytest.mark.parametrize("M", [9, 17])
+def test_marching_tets_plane(M):
+    """f = z - 0.37: every vertex lies on the plane, the triangles tile the unit square (area 1) and face +z."""
+    T = oracle.marching_tets(M, _lattice(M, lambda x, y, z: z - 0.37))
+    np.testing.assert_allclose(T[..., 2], 0.37, atol=1e-12)
+    n = np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0])
+    assert abs(0.5 * np.linalg.norm(n, axis=1).sum() - 1.0) < 1e-12
+    assert (n[:, 2] > 0).all()
+
+
+def _edges(T):
+    key = lambda v: tuple(np.round(v, 12))
+    directed = {}
+    for tri in T:
+        for a, b in ((0, 1), (1, 2), (2, 0)):
+            e = (key(tri[a]), key(tri[b]))
+            directed[e] = directed.get(e, 0) + 1
+    return directed
+
+
+def test_marching_tets_sphere_closed_oriented_and_accurate():
+    """|x - c| - r: a closed, consistently oriented surface (every directed edge once, its reverse once, Euler
+    characteristic 2) whose area and enclosed volume approach 4 pi r^2 and 4/3 pi r^3 as the lattice refines."""
+    c, r = np.array([0.5, 0.52, 0.48]), 0.3
+    errs = []
+    for M in (17, 33):
+        T = oracle.marching_tets(M, _lattice(M, lambda x, y, z: np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2
+                                                                        + (z - c[2]) ** 2) - r))
+        d = _edges(T)
+        assert all(v == 1 for v in d.values())
+        assert all((b, a) in d for (a, b) in d)
+        V = len({v for e in d for v in e}); E = len(d) // 2; F = T.shape[0]
+        assert V - E + F == 2
+        area = 0.5 * np.linalg.norm(np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0]), axis=1).sum()
+        vol = (T[:, 0] * np.cross(T[:, 1], T[:, 2])).sum() / 6.0
+        errs.append((abs(area / (4 * np.pi * r * r) - 1), abs(vol / (4 / 3 * np.pi * r ** 3) - 1)))
+    assert errs[1][0] < 0.01 and errs[1][1] < 0.01
+    assert errs[1][0] < errs[0][0] and errs[1][1] < errs[0][1]
+
+
+def test_marching_tets_empty_and_full():
+    assert oracle.marching_tets(5, np.ones(125)).shape[0] == 0
+    assert oracle.marching_tets(5, -np.ones(125)).shape[0] == 0
+
+
+def test_sample_mesh_area_weighting_and_support():
+    """Two triangles with areas 1 : 3: the samples split 1 : 3 and lie on their triangles; the mean of the
+    samples on one triangle is its centroid."""
+    T = np.array([[[0, 0, 0], [1, 0, 0], [0, 1, 0]],
+                  [[0, 0, 1], [3, 0, 1], [0, 1, 1]]], np.float32)
+    n = 40000
+    P = oracle.sample_mesh(T, n, seed=7)
+    on0 = np.abs(P[:, 2]) < 1e-12
+    on1 = np.abs(P[:, 2] - 1) < 1e-12
+    assert (on0 | on1).all()
+    frac = on0.mean()
+    assert abs(frac - 0.25) < 4 * np.sqrt(0.25 * 0.75 / n)
+    for tri, m in ((T[0], on0), (T[1], on1)):
+        Q = P[m]
+        ux, uy = tri[1, 0], tri[2, 1]
+        assert (Q[:, 0] >= -1e-12).all() and (Q[:, 1] >= -1e-12).all()
+        assert (Q[:, 0] / ux + Q[:, 1] / uy <= 1 + 1e-9).all()
+        cen = tri.astype(np.float64).mean(0)
+        sd = max(ux, uy) / np.sqrt(18)                  # the largest coordinate deviation on the triangle
+        np.testing.assert_allclose(Q.mean(0)[:2], cen[:2], atol=5 * sd / np.sqrt(m.sum()))
+
+
+def test_chamfer_closed_forms():
+    """A set against itself is 0; against a copy translated by s (much shorter than the spacing) each direction
+    sums N |s|^2; small sets match the double loop."""
+    r = rng(70)
+    g = np.stack(np.meshgrid(*[np.arange(6) / 5.0] * 3, indexing="ij"), -1).reshape(-1, 3)
+    assert oracle.chamfer(g, g) == (0.0, 0.0)
+    s = np.array([0.01, -0.02, 0.015])
+    a, b = oracle.chamfer(g, g + s)
+    np.testing.assert_allclose([a, b], [g.shape[0] * (s @ s)] * 2, rtol=1e-12)
+    A = r.random((40, 3)); B = r.random((55, 3))
+    ab = sum(min(((p - q) ** 2).sum() for q in B) for p in A)
+    ba = sum(min(((p - q) ** 2).sum() for p in A) for q in B)
+    np.testing.assert_allclose(oracle.chamfer(A, B), [ab, ba], rtol=1e-12)
+
