@@ -330,7 +330,8 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_extras:     # single-GPU runs only: the same on every N
         line["configs"] = {"fit_step_256_o2": bench_fit_step(), "query_only_256": bench_query_only(),
                            "query_pair_c_abi_256": bench_query_pair(),
-                           "render_160": bench_render(), "render_fit_160": bench_render_fit()}
+                           "render_160": bench_render(), "render_fit_160": bench_render_fit(),
+                           "recon_256_union": bench_recon()}
         if not args.no_serving:
             line["configs"]["serving"] = bench_serving()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -528,6 +529,55 @@ def bench_render(steps=5, warmup=2):
     return {"workload": "ray-march training step, 8192 rays x 256 samples, 160^3 BF16 density o2 + colour o1 (3 ch)",
             "train_ms_per_step": ms, "train_Msamples_per_s": R * S / (ms * 1e-3) / 1e6,
             "forward_ms": fwd, "forward_Msamples_per_s": R * S / (fwd * 1e-3) / 1e6}
+
+
+def bench_recon(coarse_steps=1500, fine_steps=500, n_pts=1 << 20, M=256, n_samples=1 << 16, fine_lr=1e-4):
+    """Reconstruction metrics of the union shape (24 spheres, 8 boxes) fitted coarse to fine as Sec. 4.1 trains:
+    128^3 order 2 for 1500 steps (Adam lr 5e-3), re-expanded onto 256^3 (tg_resample), 500 more steps (lr 1e-4;
+    a fresh Adam at the coarse rate adds more noise than it removes), L1 + 0.1 eikonal, 2^20 points per step. Then the paper's metrics on stand-in data: volumetric IoU on 2^20 uniform
+    points, mean |SDF error| on 2^16, and the Chamfer distance between 2^16 area-weighted points of the
+    extracted mesh (M^3 lattice, marching tetrahedra) and 2^16 points on the target surface."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    from paper_2402_14415_gb300.fit import fit_sdf
+    shape = W.union_shape(0)
+    dsh = tg.DeviceShape(shape.spheres, shape.boxes, shape.area_cdf())
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    ev = torch.rand((1 << 20, 3), device="cuda", generator=gen)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    coarse = tg.tg_create(3, 128, ORDER, 1, "f32", seed=0, init_std=1e-3)
+    fit_sdf(coarse, dsh, coarse_steps, n_pts, lr=5e-3, lambda_eik=0.1)
+    g = tg.tg_create(3, RES, ORDER, 1, "f32", seed=0, init_std=0.0)
+    tg.tg_resample(coarse, g)
+    r = fit_sdf(g, dsh, fine_steps, n_pts, lr=fine_lr, lambda_eik=0.1, seed=3, eval_pts=ev[:1 << 16],
+                eval_every=fine_steps)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    iou = tg.tg_sdf_iou(g, dsh, ev)
+    _, count = tg.tg_extract_mesh(g, M, 0.0, max_tris=0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    tris, _ = tg.tg_extract_mesh(g, M, 0.0, max_tris=count)
+    b.record()
+    torch.cuda.synchronize()
+    ms_mesh = a.elapsed_time(b)
+    gt = tg.tg_sample_sdf_points(dsh, seed=9, step=0, n=2 * n_samples, jitter=0.0)[n_samples:]
+    gt = gt[tg.tg_sdf_eval_target(dsh, gt).abs() < 1e-5].contiguous()   # drops the sampler's uniform fallbacks
+    a.record()
+    mp = tg.tg_sample_mesh(tris, n_samples, seed=10)
+    sa, sb = tg.tg_chamfer(mp, gt)
+    b.record()
+    torch.cuda.synchronize()
+    cd = sa / mp.shape[0] + sb / gt.shape[0]
+    return {"workload": f"union shape fitted coarse to fine: 128^3 order 2 for {coarse_steps} steps (Adam lr 5e-3), "
+                        f"resampled to 256^3, {fine_steps} steps (lr {fine_lr:g}); 2^20 points per step, L1 + 0.1 "
+                        f"eikonal; mesh at {M}^3 by marching tetrahedra",
+            "fit_s": fit_s, "mean_abs_sdf_error": r.final_error, "iou": iou, "triangles": count,
+            "chamfer_l2": cd, "chamfer_points": [int(mp.shape[0]), int(gt.shape[0])],
+            "mesh_extract_ms": ms_mesh, "sample_and_chamfer_ms": a.elapsed_time(b)}
 
 
 def bench_render_fit(steps=3000, res=160, R=8192, S=256, side=100, lr=(0.1, 0.03)):

@@ -367,6 +367,44 @@ TG_API tg_status tg_sdf_step(const tg_grid *grid, tg_batch *batch, const tg_shap
  * Errors: TG_EINVAL (NULL grid or coef_grad, 2-D grid, lambda < 0), TG_EDEVICE. */
 TG_API tg_status tg_tv_step(const tg_grid *grid, float lambda, float *coef_grad, float *loss_sum, tg_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Mesh extraction and the Chamfer distance (the surface metric of Sec. 4.1).
+ * ------------------------------------------------------------------------ */
+/* Triangulates the level set f = iso of channel 0 of a 3-D grid. The field is
+ * sampled on the M^3 lattice x = (i, j, k) / (M - 1) (Eq. 2 - Eq. 4), and the
+ * mesh is made by marching tetrahedra: each lattice cube is cut into the six
+ * tetrahedra around its main diagonal, a lattice point is inside where its
+ * value is below iso, crossings are linear on the lattice edges, and the
+ * triangles face increasing f. The mesh of a level set that stays inside the
+ * domain is closed. The triangles are written to tris (device, max_tris x 9
+ * floats: x, y, z of the three vertices) in a fixed order: cubes with k, then
+ * j, then i ascending, six tetrahedra per cube in a fixed order. Writes stop at
+ * max_tris, and *n_tris (device, 1 int64) receives the full count, so a call
+ * with max_tris = 0 (tris may be NULL) sizes the buffer. Allocates and frees
+ * about 4 M^3 + 12 (M - 1)^2 bytes of scratch in stream order.
+ * Errors: TG_EINVAL (NULL, 2-D grid, M outside [2, 2048]), TG_EDEVICE. */
+TG_API tg_status tg_extract_mesh(const tg_grid *grid, int M, float iso, float *tris, int64_t max_tris,
+                                 int64_t *n_tris, tg_stream stream);
+
+/* N area-weighted points (device, N x 3) on the first min(*n_tris, max_tris)
+ * triangles of tris (device, 9 floats each; n_tris a device int64, as
+ * tg_extract_mesh writes it). Sample s takes u = U(3 s) times the total area
+ * and the first triangle whose running area (summed in triangle order, FP64)
+ * exceeds it, then r1 = U(3 s + 1), r2 = U(3 s + 2) and the point
+ * (1 - sqrt r1) v0 + sqrt r1 (1 - r2) v1 + sqrt r1 r2 v2, where U is the
+ * counter-based generator (seed, stream 0x4D455348). With no triangles the
+ * points are 0. Errors: TG_EINVAL (NULL, negative sizes), TG_EDEVICE. */
+TG_API tg_status tg_sample_mesh(const float *tris, const int64_t *n_tris, int64_t max_tris, int64_t N,
+                                uint64_t seed, float *pts, tg_stream stream);
+
+/* Adds sum_{a in A} min_{b in B} |a - b|^2 to sums[0] and
+ * sum_{b in B} min_{a in A} |a - b|^2 to sums[1] (device, 2 doubles; the
+ * caller zeroes them) for point sets A (device, nA x 3) and B (nB x 3); the
+ * Chamfer distance is sums[0] / nA + sums[1] / nB. Exact nearest neighbours
+ * (brute force, FP32 distances, FP64 sums). Errors: TG_EINVAL, TG_EDEVICE. */
+TG_API tg_status tg_chamfer(const float *A, int64_t nA, const float *B, int64_t nB, double *sums,
+                            tg_stream stream);
+
 /* Accumulates sum_P |f(x) - d(x)| over N points (device, N x 3) into
  * err_sum (device, 1 float): the mean |SDF error| of a fit is err_sum / N.
  * 3-D one-channel grids. */

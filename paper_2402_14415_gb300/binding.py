@@ -96,6 +96,9 @@ _SIGS = {
     "tg_tv_step": [_vp, ctypes.c_float, _vp, _vp, _vp],
     "tg_sdf_error": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
     "tg_sdf_iou": [_vp, ctypes.POINTER(ShapeStruct), _vp, _i64, _vp, _vp],
+    "tg_extract_mesh": [_vp, _int, ctypes.c_float, _vp, _i64, _vp, _vp],
+    "tg_sample_mesh": [_vp, _vp, _i64, _i64, ctypes.c_uint64, _vp, _vp],
+    "tg_chamfer": [_vp, _i64, _vp, _i64, _vp, _vp],
     "tg_save": [_vp, ctypes.c_char_p],
     "tg_resample": [_vp, _vp, _vp],
     "tg_load": [ctypes.c_char_p, ctypes.POINTER(_vp)],
@@ -438,6 +441,42 @@ def tg_sdf_iou(grid: Grid, shape: DeviceShape, pts, stream=None) -> float:
                              _ptr(counts, "counts", torch.int64), _stream(stream)), "tg_sdf_iou")
     inter, uni = counts.tolist()
     return inter / uni if uni else 1.0
+
+
+def tg_extract_mesh(grid: Grid, M: int, iso: float = 0.0, max_tris=None, stream=None):
+    """Triangles (T, 3, 3) of the level set f = iso of channel 0 on an M^3 lattice. Without max_tris a
+    counting call sizes the buffer first (one read-back); with it, at most max_tris are kept and the full count
+    is returned beside them: (tris, count)."""
+    n = torch.zeros(1, device="cuda", dtype=torch.int64)
+    if max_tris is None:
+        _check(load().tg_extract_mesh(grid.handle, M, iso, None, 0, n.data_ptr(), _stream(stream)),
+               "tg_extract_mesh")
+        max_tris = int(n.item())
+    tris = torch.empty((max(max_tris, 1), 3, 3), device="cuda")
+    _check(load().tg_extract_mesh(grid.handle, M, iso, tris.data_ptr(), max_tris, n.data_ptr(), _stream(stream)),
+           "tg_extract_mesh")
+    count = int(n.item())
+    return tris[:min(count, max_tris)], count
+
+
+def tg_sample_mesh(tris, N: int, seed: int, stream=None):
+    """N area-weighted points (N, 3) on the triangles (T, 3, 3)."""
+    T = tris.shape[0]
+    n = torch.tensor([T], device="cuda", dtype=torch.int64)
+    pts = torch.empty((N, 3), device="cuda")
+    _check(load().tg_sample_mesh(_ptr(tris, "tris") if T else None, n.data_ptr(), T, N, seed, pts.data_ptr(),
+                                 _stream(stream)), "tg_sample_mesh")
+    return pts
+
+
+def tg_chamfer(A, B, stream=None):
+    """(sum_a min_b |a - b|^2, sum_b min_a |a - b|^2) of two device point sets (synchronises)."""
+    sums = torch.zeros(2, device="cuda", dtype=torch.float64)
+    _check(load().tg_chamfer(_ptr(A, "A") if A.shape[0] else None, A.shape[0],
+                             _ptr(B, "B") if B.shape[0] else None, B.shape[0],
+                             _ptr(sums, "sums", torch.float64), _stream(stream)), "tg_chamfer")
+    a, b = sums.tolist()
+    return a, b
 
 
 def tg_resample(src: Grid, dst: Grid, stream=None):
