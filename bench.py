@@ -329,7 +329,7 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0 and world == 1 and not args.no_extras:     # single-GPU runs only: the same on every N
         line["configs"] = {"fit_step_256_o2": bench_fit_step(), "query_only_256": bench_query_only(),
-                           "query_pair_c_abi_256": bench_query_pair(),
+                           "query_pair_c_abi_256": bench_query_pair(), "query_pair_2d_1024": bench_query_2d(),
                            "render_160": bench_render(), "render_fit_160": bench_render_fit(),
                            "recon_256_union": bench_recon()}
         if not args.no_serving:
@@ -428,9 +428,50 @@ def bench_query_only(steps=5, warmup=2):
                 tg.tg_query_binned(g, batch, out=outp)
             ms = _time_ms(step, steps, warmup)
             res[f"order{order}_{dt}"] = round(n / (ms * 1e-3) / 1e6, 1)
+            if order == 2:    # the same points presorted by brick (the sort untimed), then bin + forward timed
+                tg.tg_batch_bin(batch, P)
+                Ps = tg.tg_batch_points(batch)
+                tg.tg_batch_bin(batch, Ps)
+                outs = torch.empty_like(outp)
+
+                def step_sorted():
+                    tg.tg_batch_bin(batch, Ps)
+                    tg.tg_query_binned(g, batch, out=outs)
+                ms = _time_ms(step_sorted, steps, warmup)
+                res[f"order2_{dt}_presorted"] = round(n / (ms * 1e-3) / 1e6, 1)
+                t0 = time.perf_counter()              # the presort itself, timed: one bin and one gather
+                tg.tg_batch_bin(batch, P)
+                Ps = tg.tg_batch_points(batch)
+                torch.cuda.synchronize()
+                res[f"order2_{dt}_presort_ms"] = round(1e3 * (time.perf_counter() - t0), 3)
+                del Ps, outs
             del g
-    return {"workload": "query forward (bin + binned forward, input order), 256^3, 2^24 uniform points",
+    return {"workload": "query forward (bin + binned forward, input order), 256^3, 2^24 uniform points; "
+                        "_presorted: the points presorted by brick (sort untimed), _presort_ms: that sort",
             "unit": "Mpts/s", **res}
+
+
+def bench_query_2d(steps=5, warmup=2, res2=1024):
+    """The 2-D path: tg_query + tg_query_backward (point-parallel kernels) on 2^24 uniform points, 1024^2
+    order 2 FP32 (6 coefficients per vertex, a 25 MB grid that stays in L2)."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    n = N_POINTS
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    P = torch.rand((n, 2), device="cuda", generator=gen)
+    U = torch.randn((n, 1), device="cuda", generator=gen)
+    out = torch.empty((n, 1), device="cuda")
+    g = tg.tg_create(2, res2, 2, 1, "f32", seed=0, init_std=1.0)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    ms_f = _time_ms(lambda: tg.tg_query(g, P, out=out), steps, warmup)
+
+    def pair():
+        tg.tg_query(g, P, out=out)
+        tg.tg_query_backward(g, P, U, grad)
+    ms = _time_ms(pair, steps, warmup)
+    return {"workload": f"2-D query pair (tg_query + tg_query_backward), {res2}^2 order 2 FP32, 2^24 uniform points",
+            "unit": "Mpts/s", "forward": round(n / (ms_f * 1e-3) / 1e6, 1), "pair": round(n / (ms * 1e-3) / 1e6, 1)}
 
 
 def bench_query_pair(steps=5, warmup=2):
