@@ -216,9 +216,10 @@ TG_API tg_status tg_batch_bin(tg_batch *batch, const float *pts, int64_t N, tg_s
  * The brick kernels run in 8 launches, one per parity class of bricks (bricks
  * of a class share no vertex), and each cell's points are ordered by input
  * index before the gather, so every gradient element sums the same terms in
- * the same order on every run - as long as every 8^3-cell brick holds at most
- * 1024 of the batch's points (a larger brick is processed in rounds that
- * follow the binned order). */
+ * the same order on every run. A brick holding more than 1024 of the batch's
+ * points is processed in rounds of 1024 taken by input index (the 1024
+ * smallest, the next 1024, ...), found by a binary search over the brick per
+ * round, so such bricks cost more than in the default mode. */
 #define TG_DETERMINISTIC 2
 
 /* Same outputs as tg_query / tg_query_backward for the points last binned.

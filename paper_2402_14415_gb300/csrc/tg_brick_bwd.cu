@@ -31,13 +31,47 @@ struct BwdLayout {
 // bz mod 2) - bricks of one class share no vertex, so every gradient element
 // receives at most one reduce-add per launch, in a fixed class order - and
 // the points of every cell are ordered by input index before the gather, so
-// each vertex sums its terms in a fixed order. Bitwise reproducible whenever
-// every brick fits one round (kPChunk points): the rounds of a larger brick
-// follow the binned order, which is not fixed.
+// each vertex sums its terms in a fixed order. A brick of more than kPChunk
+// points takes its rounds by input index: round r holds the records whose
+// index lies in (k_{r-1}, k_r], k_r the ((r + 1) kPChunk)-th smallest index of
+// the brick, so what a round contains does not depend on the binned order.
 struct DetClass {
     int px, py, pz;       // parity of the bricks of this launch
     int ncx, ncy;         // bricks of the class along x and y
 };
+
+// Number of the brick's n records whose input index lies in (lo, hi], summed
+// over the block (every thread gets it). warp_sum: kBwdThreads / 32 ints.
+__device__ __forceinline__ int det_count(const float4 *__restrict__ recs, int n, int lo, int hi, int *warp_sum)
+{
+    int c = 0;
+    for (int j = threadIdx.x; j < n; j += kBwdThreads) {
+        const int k = __float_as_int(recs[j].w);
+        c += k > lo && k <= hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __syncthreads();                                   // the previous call's sums have been read
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    int total = 0;
+#pragma unroll
+    for (int w = 0; w < kBwdThreads / 32; ++w) total += warp_sum[w];
+    return total;
+}
+
+// The smallest index T > lo such that (lo, T] holds kPChunk of the brick's
+// records (more than kPChunk have an index above lo): a binary search on counts.
+__device__ __forceinline__ int det_round_end(const float4 *__restrict__ recs, int n, int lo, int *warp_sum)
+{
+    int a = lo + 1, b = 0x7fffffff - 1;                 // the answer lies in [a, b]
+    while (a < b) {
+        const int m = a + (b - a) / 2;
+        if (det_count(recs, n, lo, m, warp_sum) >= kPChunk) b = m;
+        else a = m + 1;
+    }
+    return a;
+}
 
 template <int ORDER, int C, bool HAS_G, bool IN_ORDER, bool DET>
 __global__ void __launch_bounds__(kBwdThreads)
@@ -78,10 +112,52 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
             reinterpret_cast<float4 *>(tile)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
+    const bool det_multi = DET && !single;
+    int kprev = -1;                                   // deterministic rounds: indices above kprev are left
     for (int base = p0; base < p1; base += kPChunk) {
         const int cnt = min(kPChunk, p1 - base);
+        int kend = 0x7fffffff;                        // deterministic rounds: this round's last index
+        if (det_multi && p1 - base > kPChunk) kend = det_round_end(sorted + p0, p1 - p0, kprev, ints + GatherInts::warp_tmp);
         for (int j = tid; j < kBrickCells; j += kBwdThreads) cell_cur[j] = 0;
         __syncthreads();
+        if (det_multi) {   // the round's records: two passes over the brick, counting then placing
+            for (int j = tid; j < p1 - p0; j += kBwdThreads) {
+                const float4 q = sorted[p0 + j];
+                const int key = __float_as_int(q.w);
+                if (key <= kprev || key > kend) continue;
+                const float x[3] = {q.x, q.y, q.z};
+                int c[3];
+                float t[3];
+                locate<3>(x, res, scale, c, t);
+                atomicAdd(cell_cur + (c[0] - x0) + kBrick * ((c[1] - y0) + kBrick * (c[2] - z0)), 1);
+            }
+            __syncthreads();
+            gather_scan_cells<kBwdThreads>(ints);
+            for (int j = tid; j < p1 - p0; j += kBwdThreads) {
+                const float4 q = sorted[p0 + j];
+                const int key = __float_as_int(q.w);
+                if (key <= kprev || key > kend) continue;
+                const int64_t n = IN_ORDER ? (int64_t)key : (int64_t)(p0 + j);
+                const float x[3] = {q.x, q.y, q.z};
+                int c[3];
+                float v[RS];
+                locate<3>(x, res, scale, c, v);
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) v[3 + ch] = __ldg(dLdf + n * C + ch);
+                if constexpr (HAS_G) {
+#pragma unroll
+                    for (int i = 0; i < 3 * C; ++i) v[3 + C + i] = __ldg(dLdg + n * 3 * C + i);
+                }
+#pragma unroll
+                for (int i = R::fields; i < RS; ++i) v[i] = 0.f;
+                const int pos = atomicAdd(cell_cur + (c[0] - x0) + kBrick * ((c[1] - y0) + kBrick * (c[2] - z0)), 1);
+#pragma unroll
+                for (int i = 0; i < RS; i += 4)
+                    *reinterpret_cast<float4 *>(rec + pos * RS + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                rec_key[pos] = key;
+            }
+            kprev = kend;
+        }
         int my_lc[kPPT], my_key[kPPT];
         float my_t[kPPT][3];
         float my_u[kPPT][R::fields - 3];             // upstream gradients, loaded before the cell scan
@@ -89,7 +165,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
         for (int r = 0; r < kPPT; ++r) {
             const int i = tid + r * kBwdThreads;
             my_lc[r] = -1;
-            if (i < cnt) {
+            if (i < cnt && !det_multi) {
                 const float4 q = sorted[base + i];
                 const int64_t n = IN_ORDER ? (int64_t)__float_as_int(q.w) : (int64_t)(base + i);
                 my_key[r] = __float_as_int(q.w);
@@ -107,7 +183,7 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
             }
         }
         __syncthreads();
-        gather_scan_cells<kBwdThreads>(ints);
+        if (!det_multi) gather_scan_cells<kBwdThreads>(ints);
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             if (my_lc[r] < 0) continue;

@@ -139,13 +139,19 @@ def test_binned_rejects_unsupported(tg):
         tg.tg_batch_bin(batch, torch.rand((17, 3), device="cuda"))
 
 
-@pytest.mark.parametrize("with_g", [False, True])
-def test_deterministic_backward_is_bitwise_reproducible(tg, with_g):
+@pytest.mark.parametrize("with_g,res,N,clustered", [
+    (False, 40, 60000, False),                # about 480 points per brick: every brick fits one round
+    (True, 40, 60000, False),
+    (False, 10, 60000, False),                # 8 bricks of about 7500 points: rounds taken by input index
+    (True, 26, 50000, True),                  # half the points in one corner: single- and multi-round bricks
+])
+def test_deterministic_backward_is_bitwise_reproducible(tg, with_g, res, N, clustered):
     """TG_DETERMINISTIC: the same gradient bit for bit from three independent binnings (whose binned order
     differs from run to run), and the oracle's within tolerance."""
-    res, N = 40, 60000                        # about 480 points per brick: every brick fits one round
     g = tg.tg_create(3, res, 2, 1, "f32", seed=2, init_std=0.5)
     pts = W.uniform_points(51, N)
+    if clustered:
+        pts[: N // 2] *= 0.15
     P = to_dev(pts)
     r = np.random.default_rng(52)
     up = r.normal(size=(N, 1)).astype(np.float32)
