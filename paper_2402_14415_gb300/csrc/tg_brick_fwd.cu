@@ -45,28 +45,34 @@ __device__ __forceinline__ void load_block_smem(const T *p, float *out)
     }
 }
 
-constexpr int kFwdChunk = 1024;                       // points sorted per round
-constexpr int kFwdPPT = kFwdChunk / kFwdThreads;
+// Points sorted per round. The one-channel value kernel takes 512: it fits 48
+// registers, so 5 blocks share an SM. The kernels that write spatial gradients
+// or several channels need more registers, which then set their occupancy,
+// and take 1024.
+template <bool WIDE>
+__host__ __device__ constexpr int fwd_chunk() { return WIDE ? 1024 : 512; }
 
-template <typename T, int NV>
+template <typename T, int NV, int CHUNK>
 struct FwdLayout {
     static constexpr int row = BoxInner<T, NV>::value;                 // tile row pitch (elements)
     static constexpr int tile_bytes = BoxInner<T, NV>::tile_bytes;
     static constexpr int bar_off = (tile_bytes + 15) / 16 * 16;
     static constexpr int ints_off = bar_off + 16;                    // cell counters + scan workspace
     static constexpr int rec_off = (ints_off + SortInts::total * 4 + 15) / 16 * 16;
-    static constexpr int bytes = rec_off + kFwdChunk * 16;
+    static constexpr int bytes = rec_off + CHUNK * 16;
 };
 
 template <typename T, int ORDER, int C, bool WANT_GRAD, bool IN_ORDER>
-__global__ void __launch_bounds__(kFwdThreads)
+__global__ void __launch_bounds__(kFwdThreads, (WANT_GRAD || C > 1) ? 1 : 5)
 brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int nby,
                  const float4 *__restrict__ sorted, const int *__restrict__ offsets, float *__restrict__ out,
                  float *__restrict__ gx, int *__restrict__ status)
 {
     constexpr int K = Basis<3, ORDER>::K;
     constexpr int NV = K * C;
-    using L = FwdLayout<T, NV>;
+    constexpr int kFwdChunk = fwd_chunk<WANT_GRAD || (C > 1)>();
+    constexpr int kFwdPPT = kFwdChunk / kFwdThreads;
+    using L = FwdLayout<T, NV, kFwdChunk>;
     constexpr int BXI = L::row;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *tile = reinterpret_cast<T *>(smem_raw);
@@ -187,7 +193,7 @@ struct BinnedFwd {
     {
         constexpr int NV = Basis<3, ORDER>::K * C;
         auto k = brick_fwd_kernel<T, ORDER, C, WANT_GRAD, IN_ORDER>;
-        const int smem = FwdLayout<T, NV>::bytes;
+        const int smem = FwdLayout<T, NV, fwd_chunk<WANT_GRAD || (C > 1)>()>::bytes;
         tg_status st = set_smem((const void *)k, smem);
         if (st != TG_OK) return st;
         k<<<(unsigned)bt->nbricks, kFwdThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted, bt->offsets,
@@ -206,7 +212,7 @@ struct BinnedFwd {
             const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                            : (g->dtype == TG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-            tg_status st = make_brick_map(&map, g->store, dt, (int)sizeof(T), g->res, NV, FwdLayout<T, NV>::row, kBV);
+            tg_status st = make_brick_map(&map, g->store, dt, (int)sizeof(T), g->res, NV, BoxInner<T, NV>::value, kBV);
             if (st != TG_OK) return st;
             if (gx) return in_order ? launch<true, true, ORDER, C>(map, g, bt, out, gx, s)
                                     : launch<true, false, ORDER, C>(map, g, bt, out, gx, s);
