@@ -492,7 +492,13 @@ typedef struct {
     float lambda_tv;            /* total variation weight (tg_tv_step); 0: off */
 } tg_fit_desc;
 
-typedef enum { TG_JOB_QUEUED = 0, TG_JOB_RUNNING = 1, TG_JOB_DONE = 2, TG_JOB_FAILED = 3 } tg_job_state;
+typedef enum {
+    TG_JOB_QUEUED = 0,
+    TG_JOB_RUNNING = 1,
+    TG_JOB_DONE = 2,
+    TG_JOB_FAILED = 3,
+    TG_JOB_CANCELLED = 4
+} tg_job_state;
 
 typedef struct {
     int state;                  /* tg_job_state */
@@ -530,6 +536,15 @@ TG_API tg_status tg_server_grid(tg_server *server, tg_job_id id, tg_grid **grid)
 
 /* Frees a finished fit job's grid (or a finished query's record). TG_EBUSY if it is still running. */
 TG_API tg_status tg_release(tg_server *server, tg_job_id id);
+
+/* Cancels a job. A queued job leaves the queue at once. A running fit job
+ * stops at its next step boundary (no kernel is interrupted): the server step
+ * that sees its last step retired marks it TG_JOB_CANCELLED and frees its
+ * scratch, while its grid - the fit so far - stays resident, and queries can
+ * still use it, until tg_release. A query that has been launched cannot be
+ * recalled (TG_EBUSY). Finished jobs are left as they are.
+ * Errors: TG_EINVAL (NULL), TG_ENOTFOUND, TG_EBUSY. */
+TG_API tg_status tg_cancel(tg_server *server, tg_job_id id);
 
 /* Admission order of queued fit jobs: arrival order (default), or the job
  * with the fewest device bytes first (short jobs overtake long ones; queries

@@ -110,6 +110,7 @@ _SIGS = {
     "tg_poll": [_vp, _i64, ctypes.POINTER(JobResult)],
     "tg_server_grid": [_vp, _i64, ctypes.POINTER(_vp)],
     "tg_release": [_vp, _i64],
+    "tg_cancel": [_vp, _i64],
     "tg_server_set_policy": [_vp, _int],
     "tg_render_rays": [_vp, _vp, _vp, _vp, _i64, _int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_float, _vp, _vp,
                        _vp, _vp, _vp, _vp, _vp],
@@ -529,7 +530,7 @@ def tg_render_rays_backward(density: Grid, color: Grid, rays_o, rays_d, dL_drgb,
     return out
 
 
-JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
 
 
 class Server:
@@ -589,6 +590,10 @@ class Server:
     def release(self, jid: int):
         _check(load().tg_release(self._h, jid), "tg_release")
         self._keep.pop(jid, None)
+
+    def cancel(self, jid: int):
+        """Cancels a queued job at once, a running fit job at its next step boundary."""
+        _check(load().tg_cancel(self._h, jid), "tg_cancel")
 
     def time(self) -> float:
         return load().tg_server_time(self._h)

@@ -73,6 +73,7 @@ struct Job {
     cudaEvent_t event = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool in_flight = false;
+    bool cancel = false;             // stop at the next step boundary
     ShapeView sv{};
     // query
     tg_job_id grid_of = 0;
@@ -328,6 +329,14 @@ tg_status tg_server_step(tg_server *s, int *pending)
             free_fit_scratch(j);
         }
     }
+    // cancelled fit jobs whose last step has retired stop here; their grid stays until tg_release
+    for (auto &kv : s->jobs) {
+        Job *j = kv.second;
+        if (j->kind != 0 || j->state != TG_JOB_RUNNING || j->in_flight || !j->cancel) continue;
+        j->state = TG_JOB_CANCELLED;
+        j->t_done = s->now();
+        free_fit_scratch(j);
+    }
     for (auto &kv : s->jobs)
         if (kv.second->kind == 0 && kv.second->state == TG_JOB_RUNNING) ++running;
     // 2. admission scan over the queue: arrival order, or (TG_ADMIT_SMALLEST)
@@ -353,7 +362,7 @@ tg_status tg_server_step(tg_server *s, int *pending)
                 keep.push_back(id);
                 continue;
             }
-            if (!g || g->state == TG_JOB_FAILED || !g->grid) {
+            if (!g || g->state == TG_JOB_FAILED || !g->grid) {     // also a fit job cancelled before it ran
                 j->state = TG_JOB_FAILED;
                 j->t_done = s->now();
                 continue;
@@ -439,6 +448,26 @@ tg_status tg_server_grid(tg_server *s, tg_job_id id, tg_grid **grid)
     if (it == s->jobs.end() || it->second->kind != 0 || !it->second->grid)
         return fail(TG_ENOTFOUND, "tg_server_grid: no resident grid for job %lld", (long long)id);
     *grid = it->second->grid;
+    return TG_OK;
+}
+
+tg_status tg_cancel(tg_server *s, tg_job_id id)
+{
+    if (!s) return fail(TG_EINVAL, "tg_cancel: server is NULL");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end()) return fail(TG_ENOTFOUND, "tg_cancel: no job %lld", (long long)id);
+    Job *j = it->second;
+    if (j->state == TG_JOB_QUEUED) {
+        s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), id), s->queue.end());
+        j->state = TG_JOB_CANCELLED;
+        j->t_done = s->now();
+        return TG_OK;
+    }
+    if (j->state == TG_JOB_RUNNING) {
+        if (j->kind == 1) return fail(TG_EBUSY, "tg_cancel: the query has been launched");
+        j->cancel = true;
+    }
     return TG_OK;
 }
 

@@ -126,3 +126,34 @@ def test_fit_job_with_weight_and_tv(tg):
     # Eq. 7 leaves the far field loose, so the mixed evaluation points stop short of tol: all 200 steps run
     start = float(np.abs(W.sphere_shape().sdf(W.sdf_points(W.sphere_shape(), seed=1, step=0, n=1 << 14))).mean())
     assert r["state"] == "done" and r["steps"] == 200 and 0 <= r["error"] < start / 2, (r, start)
+
+
+def test_cancellation(tg):
+    """A queued job leaves at once; a running fit job stops at a step boundary with its partial grid resident
+    (queries still run on it) and its budget held until release; the other jobs are unaffected."""
+    kw = dict(res=48, order=2, points_per_step=1 << 12, eval_points=1 << 12, eval_every=10, max_steps=400, tol=0.0)
+    srv = tg.Server(budget_bytes=8 << 30, max_running=1)
+    a, b, c = (srv.fit_job(*shape_args(W.sphere_shape()), seed=k, **kw) for k in range(3))
+    srv.cancel(c)                                  # still queued
+    assert srv.poll(c)["state"] == "cancelled" and srv.poll(c)["steps"] == 0
+    for _ in range(100000):
+        srv.step()
+        if srv.poll(a)["steps"] >= 20:
+            break
+    srv.cancel(a)                                  # running: stops at the next step boundary
+    for _ in range(1000):
+        srv.step()
+        if srv.poll(a)["state"] != "running":
+            break
+    ra = srv.poll(a)
+    assert ra["state"] == "cancelled" and 20 <= ra["steps"] < 400, ra
+    pts = torch.rand((1000, 3), device="cuda")
+    out = torch.empty((1000, 1), device="cuda")
+    q = srv.query_job(a, pts, out)                 # the partial fit stays queryable
+    srv.run_until_idle(timeout_s=120)
+    assert srv.poll(q)["state"] == "done" and torch.isfinite(out).all()
+    assert srv.poll(b)["state"] == "done" and srv.poll(b)["steps"] == 400
+    srv.cancel(b)                                  # finished: left as it is
+    assert srv.poll(b)["state"] == "done"
+    for j in (a, b, c, q):
+        srv.release(j)

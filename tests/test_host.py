@@ -64,6 +64,16 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
         f = getattr(lib, fn)
         f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         assert f(None, None, 1, None, None) == 1
+    lib.tg_cancel.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert lib.tg_cancel(None, 1) == 1
+    for fn, args in (("tg_extract_mesh", [ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),):
+        f = getattr(lib, fn)
+        f.argtypes = args
+        assert f(None, 16, 0.0, None, 0, None, None) == 1
+    lib.tg_chamfer.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                               ctypes.c_void_p]
+    assert lib.tg_chamfer(None, 1, None, 1, None, None) == 1
 
 
 def test_product_path_has_no_oracle_reference():
