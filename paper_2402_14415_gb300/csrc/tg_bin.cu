@@ -20,7 +20,6 @@ namespace tg {
 constexpr int kBinThreads = 256;
 constexpr int kHistThreads = 1024;
 constexpr int kMaxSmemBins = 32768;   // 128 KB of shared counters
-constexpr int kColScanBricks = 32;    // bricks per block of the chunk-column scan
 constexpr int kCoarse = 64;           // bricks per coarse bin of the two-pass scatter
 constexpr int kFineThreads = 512;
 
@@ -82,71 +81,90 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tmp, int &t
     return excl;
 }
 
-// Column scan: for kColScanBricks bricks per block, the exclusive scan over
-// the G chunk histograms (in place, through shared memory so that every
-// global access is a coalesced row segment) and the brick totals.
-__global__ void __launch_bounds__(1024)
+// Column scan: one thread per brick turns the G chunk histograms of its
+// column into exclusive per-chunk offsets (in place) and writes the brick's
+// total. Neighbouring threads read neighbouring bricks, so every row access
+// of a warp is one coalesced segment; kColUnroll rows are loaded before any is
+// used, so that many loads per thread are in flight (the histograms were just
+// written and sit in L2).
+constexpr int kColUnroll = 16;
+__global__ void __launch_bounds__(kBinThreads)
 bin_chunk_scan_kernel(int *__restrict__ hist, int G, int nbricks, int *__restrict__ totals)
 {
-    extern __shared__ int tile[];          // G x kColScanBricks
-    const int b0 = blockIdx.x * kColScanBricks;
-    const int nb = min(kColScanBricks, nbricks - b0);
-    for (int j = threadIdx.x; j < G * kColScanBricks; j += blockDim.x) {
-        const int g = j / kColScanBricks, c = j % kColScanBricks;
-        tile[j] = c < nb ? hist[(int64_t)g * nbricks + b0 + c] : 0;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int c = wid; c < nb; c += blockDim.x >> 5) {   // one warp per brick column
-        int carry = 0;
-        for (int g0 = 0; g0 < G; g0 += 32) {
-            const int g = g0 + lane;
-            const int v = g < G ? tile[g * kColScanBricks + c] : 0;
-            int incl = v;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbricks) return;
+    int *col = hist + b;
+    int carry = 0, g = 0;
+    for (; g + kColUnroll <= G; g += kColUnroll) {
+        int v[kColUnroll];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
-            }
-            if (g < G) tile[g * kColScanBricks + c] = carry + incl - v;
-            carry += __shfl_sync(0xffffffffu, incl, 31);
+        for (int k = 0; k < kColUnroll; ++k) v[k] = col[(int64_t)(g + k) * nbricks];
+#pragma unroll
+        for (int k = 0; k < kColUnroll; ++k) {
+            col[(int64_t)(g + k) * nbricks] = carry;
+            carry += v[k];
         }
-        if (lane == 0) totals[b0 + c] = carry;
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < G * kColScanBricks; j += blockDim.x) {
-        const int g = j / kColScanBricks, c = j % kColScanBricks;
-        if (c < nb) hist[(int64_t)g * nbricks + b0 + c] = tile[j];
+    for (; g < G; ++g) {
+        const int v = col[(int64_t)g * nbricks];
+        col[(int64_t)g * nbricks] = carry;
+        carry += v;
     }
+    totals[b] = carry;
 }
 
 // Single-block exclusive scan of counts[0..n) into offsets[0..n] (offsets[n] =
-// total) and optionally cursor; each thread owns a contiguous run per tile.
+// total) and optionally cursor; each thread owns a contiguous run of 16 per
+// tile, moved as four 16-byte vectors where the run is whole and all three
+// arrays start on a 16-byte boundary (scalar accesses otherwise).
 __global__ void __launch_bounds__(1024)
 bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int *__restrict__ cursor, int n)
 {
     __shared__ int warp_tmp[32];
     constexpr int PER = 16;
+    const bool aligned = (((uintptr_t)counts | (uintptr_t)offsets | (uintptr_t)cursor) & 15) == 0;
     int carry = 0;
     const int per_tile = PER * blockDim.x;
     for (int base = 0; base < n; base += per_tile) {
         const int j0 = base + PER * threadIdx.x;
+        const bool whole = aligned && j0 + PER <= n;
         int v[PER];
         int sum = 0;
+        if (whole) {
 #pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            v[k] = (j0 + k < n) ? counts[j0 + k] : 0;
-            sum += v[k];
+            for (int k = 0; k < PER / 4; ++k) {
+                const int4 q = reinterpret_cast<const int4 *>(counts + j0)[k];
+                v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) v[k] = (j0 + k < n) ? counts[j0 + k] : 0;
         }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) sum += v[k];
         int total;
         int run = carry + block_exclusive_scan(sum, warp_tmp, total);
+        int o[PER];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (j0 + k < n) {
-                offsets[j0 + k] = run;
-                if (cursor) cursor[j0 + k] = run;
-            }
+            o[k] = run;
             run += v[k];
+        }
+        if (whole) {
+#pragma unroll
+            for (int k = 0; k < PER / 4; ++k) {
+                const int4 q = make_int4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+                reinterpret_cast<int4 *>(offsets + j0)[k] = q;
+                if (cursor) reinterpret_cast<int4 *>(cursor + j0)[k] = q;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                if (j0 + k < n) {
+                    offsets[j0 + k] = o[k];
+                    if (cursor) cursor[j0 + k] = o[k];
+                }
+            }
         }
         carry += total;
     }
@@ -595,7 +613,6 @@ tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
     if (st == TG_OK && b->G) {
         const int bytes = (int)(b->nbricks * sizeof(int));
         st = set_smem((const void *)bin_hist_kernel, bytes);
-        if (st == TG_OK) st = set_smem((const void *)bin_chunk_scan_kernel, b->G * kColScanBricks * (int)sizeof(int));
         if (st == TG_OK) st = set_smem((const void *)bin_coarse_place_kernel, (int)sizeof(CoarseSmem));
         if (st == TG_OK) st = set_smem((const void *)bin_fine_place_kernel, (int)sizeof(FineSmem));
     }
@@ -634,8 +651,8 @@ tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream strea
         const int smem = nbr * (int)sizeof(int);
         bin_hist_kernel<<<b->G, kHistThreads, smem, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist);
         if ((st = launch_status("tg_batch_bin: histogram")) != TG_OK) return st;
-        bin_chunk_scan_kernel<<<(nbr + kColScanBricks - 1) / kColScanBricks, 1024,
-                                b->G * kColScanBricks * sizeof(int), s>>>(b->hist, b->G, nbr, b->counts);
+        bin_chunk_scan_kernel<<<(nbr + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(b->hist, b->G, nbr,
+                                                                                            b->counts);
         if ((st = launch_status("tg_batch_bin: chunk scan")) != TG_OK) return st;
         bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, nullptr, nbr);
         if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;

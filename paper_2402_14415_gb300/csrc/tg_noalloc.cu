@@ -12,9 +12,9 @@ namespace tg {
 constexpr int64_t kNoallocMaxPoints = (int64_t)1 << 18;     // 262144 points per call
 constexpr int64_t kNoallocMaxBricks = 32768;                // res <= 257
 
-struct NoallocScratch {
-    int counts[kNoallocMaxBricks + 1];
-    int offsets[kNoallocMaxBricks + 1];
+struct NoallocScratch {      // every array starts on a 16-byte boundary
+    int counts[kNoallocMaxBricks + 4];
+    int offsets[kNoallocMaxBricks + 4];
     int cursor[kNoallocMaxBricks];
     int status[4];
     float4 sorted[kNoallocMaxPoints];
