@@ -596,7 +596,7 @@ tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
         b->nb[d] = (res - 1 + kBrick - 1) / kBrick;
         b->nbricks *= b->nb[d];
     }
-    b->G = b->nbricks <= kMaxSmemBins ? num_sms() : 0;
+    b->G = b->nbricks <= kMaxSmemBins ? kBinChunksPerSm * num_sms() : 0;
     tg_status st = cuda_status(cudaMalloc(&b->counts, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->offsets, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMalloc(&b->cursor, b->nbricks * sizeof(int)), "tg_batch_create");

@@ -34,6 +34,7 @@ tg_status cuda_status(cudaError_t e, const char *what);
 tg_status launch_status(const char *what);
 
 int num_sms();                      // SM count of the current device (cached per device)
+constexpr int kBinChunksPerSm = 1;  // point chunks of the binning per SM (one histogram row each; 2 measured slower)
 // Resident blocks per SM of a kernel at a launch shape (cached per device and kernel).
 int blocks_per_sm(const void *kernel, int threads, size_t smem);
 

@@ -96,7 +96,7 @@ static size_t fit_bytes(const tg_fit_desc &d)
     const size_t nb = (size_t)((d.res - 2) / 8 + 1);
     const size_t bricks = nb * nb * nb;
     b += (size_t)d.points_per_step * (16 + 16 + 4 + 4 * 11);                  // records, coarse, perm, staging
-    b += bricks * (3 * 4 + (bricks <= 32768 ? 4 * 152 : 0));                  // offsets and chunk histograms
+    b += bricks * (3 * 4 + (bricks <= 32768 ? 4 * kBinChunksPerSm * num_sms() : 0));   // offsets, chunk histograms
     b += (size_t)d.eval_points * 12 + 4096;
     return b;
 }
