@@ -63,7 +63,7 @@ struct FwdLayout {
 };
 
 template <typename T, int ORDER, int C, bool WANT_GRAD, bool IN_ORDER>
-__global__ void __launch_bounds__(kFwdThreads, (WANT_GRAD || C > 1) ? 1 : 5)
+__global__ void __launch_bounds__(kFwdThreads, (WANT_GRAD || C > 1) ? 0 : 5)
 brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int nby,
                  const float4 *__restrict__ sorted, const int *__restrict__ offsets, float *__restrict__ out,
                  float *__restrict__ gx, int *__restrict__ status)
