@@ -776,8 +776,8 @@ def profile_once():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # full-size launch captured by `ncu --set full ... python bench.py --profile`
 # (profiles/query_step_256_o2_2e24_full.md); None once the kernel has changed since.
-TRAFFIC = {"forward": 1.200345e9 + 0.381539e9, "backward": 1.562404e9 + 0.638993e9,
-           "bin": (0.201361 + 0.003306 + 0.019937 + 0.000140 + 0.228013 + 0.222032 + 0.275145 + 0.294213) * 1e9}
+TRAFFIC = {"forward": 1.200449e9 + 0.381682e9, "backward": 1.562584e9 + 0.639463e9,
+           "bin": (0.201360 + 0.003243 + 0.019930 + 0.000140 + 0.228140 + 0.221858 + 0.275141 + 0.294243) * 1e9}
 KERNEL_NAMES = {"bin": "bin_* (5 kernels, tg_batch_bin)", "forward": "brick_fwd_kernel (tg_query_binned)",
                 "backward": "brick_bwd_kernel (tg_query_backward_binned)"}
 
