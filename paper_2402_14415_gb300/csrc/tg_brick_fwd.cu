@@ -97,7 +97,6 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
     }
 
     const float scale = (float)(res - 1), h = 1.0f / (float)(res - 1);
-    const uint64_t keep = IN_ORDER ? l2_keep_policy() : 0;     // L2 policy of the input-order writes
     bool waited = false;
     for (int base = p0; base < p1; base += kFwdChunk) {
         const int cnt = min(kFwdChunk, p1 - base);
@@ -175,15 +174,10 @@ brick_fwd_kernel(const __grid_constant__ CUtensorMap cmap, int res, int nbx, int
             });
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
-                // input order: random 4-byte writes, kept in L2 so that a sector's writes merge there
-                if (IN_ORDER) st_l2_hint(out + n * C + ch, f[ch], keep);
-                else out[n * C + ch] = f[ch];
+                out[n * C + ch] = f[ch];
                 if constexpr (WANT_GRAD) {
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        if (IN_ORDER) st_l2_hint(gx + (n * C + ch) * 3 + d, gu[ch][d], keep);
-                        else gx[(n * C + ch) * 3 + d] = gu[ch][d];
-                    }
+                    for (int d = 0; d < 3; ++d) gx[(n * C + ch) * 3 + d] = gu[ch][d];
                 }
             }
         }

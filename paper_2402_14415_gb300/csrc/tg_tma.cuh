@@ -22,21 +22,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// L2 cache policy that keeps the lines it touches in L2 ahead of normal
-// traffic (PTX createpolicy, evict_last for the whole access).
-__device__ __forceinline__ uint64_t l2_keep_policy()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-// Store of one float under an L2 cache policy.
-__device__ __forceinline__ void st_l2_hint(float *ptr, float v, uint64_t policy)
-{
-    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(ptr), "f"(v), "l"(policy) : "memory");
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
