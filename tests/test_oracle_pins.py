@@ -714,3 +714,32 @@ def test_chamfer_closed_forms():
     ba = sum(min(((p - q) ** 2).sum() for p in A) for q in B)
     np.testing.assert_allclose(oracle.chamfer(A, B), [ab, ba], rtol=1e-12)
 
+
+# --------------------------------------------------------------------------
+# The tolerance scale of the parity tests: sum_i w_i sum_k |theta_ik phi_k|
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,order,C", [(3, 2, 1), (3, 1, 3), (2, 2, 2)])
+def test_absscale_bounds_the_value_and_is_exact_for_nonnegative_terms(dim, order, C):
+    """It is never below |f| (triangle inequality), equals f when every term is non-negative (order 0 with
+    non-negative coefficients, and order 2 with only non-negative value and diagonal-Hessian coefficients),
+    and scales linearly with the coefficients."""
+    res = 6
+    r = rng(80 + dim + order)
+    K = W.n_coefs(dim, order)
+    coefs = r.normal(size=res ** dim * C * K)
+    pts = r.random((300, dim)).astype(np.float32)
+    f, _, _, _ = oracle.query(dim, res, order, C, coefs, pts, want_grad=False)
+    S = oracle.query_absscale(dim, res, order, C, coefs, pts)
+    assert (S >= np.abs(f).reshape(S.shape) - 1e-12).all()
+    np.testing.assert_allclose(oracle.query_absscale(dim, res, order, C, 3.0 * coefs, pts), 3.0 * S, rtol=1e-12)
+    pos = np.abs(r.normal(size=res ** dim * C))
+    f0, _, _, _ = oracle.query(dim, res, 0, C, pos, pts, want_grad=False)
+    np.testing.assert_allclose(oracle.query_absscale(dim, res, 0, C, pos, pts), f0.reshape(-1, C), rtol=1e-12)
+    if order == 2:                              # value and diagonal Hessian terms only: every term >= 0
+        q = np.zeros((res ** dim * C, K))
+        q[:, 0] = np.abs(r.normal(size=q.shape[0]))
+        q[:, 1 + dim:1 + 2 * dim] = np.abs(r.normal(size=(q.shape[0], dim)))
+        q = q.reshape(-1)
+        fq, _, _, _ = oracle.query(dim, res, 2, C, q, pts, want_grad=False)
+        np.testing.assert_allclose(oracle.query_absscale(dim, res, 2, C, q, pts), fq.reshape(-1, C), rtol=1e-12)
+
