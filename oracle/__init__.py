@@ -54,6 +54,7 @@ def lib():
             L.tgo_query.argtypes = [i32, i32, i32, i32, _f64p, i64, _f32p, _f64p, _f64p, _i32p, _f64p]
             L.tgo_query_backward.argtypes = [i32, i32, i32, i32, i64, _f32p, _f64p, _f64p, _f64p, _f64p]
             L.tgo_query_absscale.argtypes = [i32, i32, i32, i32, _f64p, i64, _f32p, _f64p]
+            L.tgo_query_gradscale.argtypes = [i32, i32, i32, i32, _f64p, i64, _f32p, _f64p]
             L.tgo_adam.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64]
             L.tgo_adam_lazy.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64]
             L.tgo_sdf_union.argtypes = [i32, _f32p, i32, _f32p, _f64p]; L.tgo_sdf_union.restype = f64
@@ -127,6 +128,16 @@ def query_absscale(dim, res, order, C, coefs, pts):
     s = np.zeros((pts.shape[0], C))
     lib().tgo_query_absscale(dim, res, order, C, _p(_c(coefs, np.float64), _f64p), pts.shape[0],
                              _p(pts, _f32p), _p(s, _f64p))
+    return s
+
+
+def query_gradscale(dim, res, order, C, coefs, pts):
+    """Per point, channel and axis: the magnitude of the terms of the world-unit spatial gradient,
+    sum_i |d w_i / d x_a| sum_k |theta_k phi_k| + w_i sum_k |theta_k d phi_k / d delta_a|  (N, C, dim)."""
+    pts = _c(pts, np.float32).reshape(-1, dim)
+    s = np.zeros((pts.shape[0], C, dim))
+    lib().tgo_query_gradscale(dim, res, order, C, _p(_c(coefs, np.float64), _f64p), pts.shape[0],
+                              _p(pts, _f32p), _p(s, _f64p))
     return s
 
 

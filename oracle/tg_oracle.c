@@ -356,6 +356,42 @@ TGO_API void tgo_query_absscale(int dim, int res, int order, int C, const double
     }
 }
 
+/* Per-point, per-axis scale of the world-unit spatial gradient for the
+ * tolerance: d f / d x_a = sum_i (d w_i / d x_a) T_i + w_i d T_i / d x_a
+ * (Eq. 3 and Eq. 4 differentiated), so the magnitude of the terms its FP32
+ * sum cancels is
+ *   sum_i |d w_i / d x_a| sum_k |theta_k phi_k| + w_i sum_k |theta_k d phi_k / d delta_a|
+ * with d w / d x = (res - 1) d w / d t and delta = x - v_i in world units. */
+TGO_API void tgo_query_gradscale(int dim, int res, int order, int C, const double *coefs, int64_t N,
+                                 const float *pts, double *scale)
+{
+    int K = tgo_num_coefs(dim, order);
+    double h = 1.0 / (double)(res - 1);
+    #pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        int cell[3]; double t[3];
+        tgo_locate(dim, res, pts + n * dim, cell, t);
+        for (int ch = 0; ch < C; ++ch) {
+            double s[3] = {0, 0, 0};
+            for (int i = 0; i < (1 << dim); ++i) {
+                double delta[3] = {0, 0, 0}, phi[10], dphi[10][3];
+                for (int d = 0; d < dim; ++d) delta[d] = (t[d] - (double)((i >> d) & 1)) * h;
+                series_jacobian(dim, order, delta, phi);
+                series_jacobian_grad(dim, order, delta, dphi);
+                const double *th = coefs + (vertex_index(dim, res, cell, i) * C + ch) * K;
+                double w = corner_weight(dim, i, t), tsum = 0;
+                for (int k = 0; k < K; ++k) tsum += fabs(th[k] * phi[k]);
+                for (int a = 0; a < dim; ++a) {
+                    double dsum = 0;
+                    for (int k = 0; k < K; ++k) dsum += fabs(th[k] * dphi[k][a]);
+                    s[a] += fabs(corner_weight_grad(dim, i, t, a) / h) * tsum + w * dsum;
+                }
+            }
+            for (int a = 0; a < dim; ++a) scale[(n * C + ch) * dim + a] = s[a];
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Optimiser. The paper fixes only the learning rate (Sec. 4.1); the build   */
 /* uses Adam (Kingma & Ba 2015, Algorithm 1) with bias correction, step >= 1. */

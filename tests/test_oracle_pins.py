@@ -743,3 +743,33 @@ def test_absscale_bounds_the_value_and_is_exact_for_nonnegative_terms(dim, order
         fq, _, _, _ = oracle.query(dim, res, 2, C, q, pts, want_grad=False)
         np.testing.assert_allclose(oracle.query_absscale(dim, res, 2, C, q, pts), fq.reshape(-1, C), rtol=1e-12)
 
+
+
+# --------------------------------------------------------------------------
+# The spatial-gradient tolerance scale:
+# sum_i |d w_i / d x_a| sum_k |theta_ik phi_k| + w_i sum_k |theta_ik d phi_k / d x_a|
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,order,C", [(3, 2, 1), (3, 1, 3), (2, 2, 2), (3, 0, 1)])
+def test_gradscale_bounds_the_spatial_gradient_and_is_exact_for_coherent_terms(dim, order, C):
+    """G_a is never below |d f / d x_a| (triangle inequality over the terms of Eq. 4 differentiated), scales
+    linearly with the coefficients, and equals |d f / d x_a| for an order-0 field whose vertex values are +|r|
+    at odd and -|r| at even coordinates along a: inside a cell the two corners along a then carry opposite
+    values and opposite weight slopes, so every term of the sum has the same sign."""
+    res = 6
+    r = rng(90 + dim + order)
+    K = W.n_coefs(dim, order)
+    coefs = r.normal(size=res ** dim * C * K)
+    pts = r.random((300, dim)).astype(np.float32)
+    _, gx, _, _ = oracle.query(dim, res, order, C, coefs, pts)
+    G = oracle.query_gradscale(dim, res, order, C, coefs, pts)
+    assert G.shape == gx.shape
+    assert (G >= np.abs(gx) - 1e-9 * (1 + G)).all()
+    assert (G > 1.5 * np.abs(gx)).any()                 # random signs do cancel somewhere
+    np.testing.assert_allclose(oracle.query_gradscale(dim, res, order, C, -2.0 * coefs, pts), 2.0 * G, rtol=1e-12)
+    j = np.stack(np.meshgrid(*[np.arange(res)] * dim, indexing="ij")[::-1], -1).reshape(-1, dim)  # x fastest
+    for a in range(dim):
+        sign = np.where(j[:, a] % 2 == 1, 1.0, -1.0)
+        f0 = (sign[:, None] * np.abs(r.normal(size=(res ** dim, C)))).reshape(-1)
+        _, g0, _, _ = oracle.query(dim, res, 0, C, f0, pts)
+        G0 = oracle.query_gradscale(dim, res, 0, C, f0, pts)
+        np.testing.assert_allclose(G0[..., a], np.abs(g0[..., a]), rtol=1e-12)
