@@ -67,7 +67,7 @@ def lib():
             L.tgo_sample_mesh.argtypes = [i64, _f32p, i64, u64, u64, _f64p]
             L.tgo_ray_box.argtypes = [_f64p, _f64p, _f64p, _f64p]; L.tgo_ray_box.restype = i32
             L.tgo_render.argtypes = [i32, i32, _f64p, i32, _f64p, i64, i32, _f32p, _f32p, u64, u64, f64,
-                                     _f64p, _f32p, _f64p, _f64p, _f64p]
+                                     _f64p, _f32p, _f64p, _f64p, _f64p, _f64p, _f64p]
             L.tgo_render_blobs.argtypes = [i32, _f64p, _f64p, _f64p, _f64p, i64, _f32p, _f32p, i32, f64, _f64p]
             _lib = L
     return _lib
@@ -249,19 +249,26 @@ def ray_box(o, d):
     return bool(hit), n.value, f.value
 
 
-def render(res, od, dcoef, oc, ccoef, rays_o, rays_d, S, seed, ray_base=0, bg=1.0, target=None):
-    """Returns rgb (R,3) and, if target is given, (loss, density grad, colour grad)."""
+def render(res, od, dcoef, oc, ccoef, rays_o, rays_d, S, seed, ray_base=0, bg=1.0, target=None, want_abs=False):
+    """Returns rgb (R,3) and, if target is given, (loss, density grad, colour grad) and, with want_abs, the
+    per-coefficient magnitudes of the terms of both gradients (density, colour)."""
     rays_o = _c(rays_o, np.float32).reshape(-1, 3); rays_d = _c(rays_d, np.float32).reshape(-1, 3)
     R = rays_o.shape[0]
     rgb = np.zeros((R, 3))
-    dg = np.zeros(res ** 3 * num_coefs(3, od)) if target is not None else None
-    cg = np.zeros(res ** 3 * 3 * num_coefs(3, oc)) if target is not None else None
+    train = target is not None
+    dg = np.zeros(res ** 3 * num_coefs(3, od)) if train else None
+    cg = np.zeros(res ** 3 * 3 * num_coefs(3, oc)) if train else None
+    da = np.zeros_like(dg) if train and want_abs else None
+    ca = np.zeros_like(cg) if train and want_abs else None
     loss = np.zeros(1)
     lib().tgo_render(res, od, _p(_c(dcoef, np.float64), _f64p), oc, _p(_c(ccoef, np.float64), _f64p), R, S,
                      _p(rays_o, _f32p), _p(rays_d, _f32p), seed, ray_base, bg, _p(rgb, _f64p),
-                     _p(_c(target, np.float32), _f32p), _p(dg, _f64p), _p(cg, _f64p), _p(loss, _f64p))
-    if target is None:
+                     _p(_c(target, np.float32), _f32p), _p(dg, _f64p), _p(cg, _f64p), _p(loss, _f64p),
+                     _p(da, _f64p), _p(ca, _f64p))
+    if not train:
         return rgb
+    if want_abs:
+        return rgb, float(loss[0]), dg, cg, da, ca
     return rgb, float(loss[0]), dg, cg
 
 

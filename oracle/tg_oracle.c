@@ -745,11 +745,52 @@ TGO_API int tgo_ray_box(const double *o, const double *d, double *near_, double 
     return 1;
 }
 
+/* Sample positions of a ray, by a normative FP32 rule (as the index rule of
+ * Eq. 2 is), so that both sides evaluate the same points: the slab test in
+ * FP32 (IEEE division), step = fl32(fl32(far - near) / S),
+ * t_i = fl32(near + fl32(fl32(i + xi_i) * step)), x = fma(t_i, d, o) rounded
+ * once to FP32, and delta_i = fl32(t_{i+1} - t_i) with t_S = far. Returns 0
+ * for a ray that misses the cube. */
+static int ray_samples_f32(const float *o, const float *d, int S, uint64_t seed, uint64_t stream, float *xs,
+                           double *del)
+{
+    float tn = 0.0f, tf = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0f) {
+            if (o[a] < 0.0f || o[a] > 1.0f) return 0;
+            continue;
+        }
+        volatile float t0 = (0.0f - o[a]) / d[a], t1 = (1.0f - o[a]) / d[a];
+        float lo = t0 < t1 ? t0 : t1, hi = t0 < t1 ? t1 : t0;
+        if (lo > tn) tn = lo;
+        if (hi < tf) tf = hi;
+    }
+    if (!(tf > tn)) return 0;
+    volatile float span = tf - tn;
+    volatile float step = span / (float)S;
+    float tprev = 0.0f;
+    for (int i = 0; i <= S; ++i) {
+        float ti = tf;
+        if (i < S) {
+            volatile float k = (float)i + (float)tgo_uniform(seed, stream, (uint64_t)i);
+            volatile float off = k * step;
+            volatile float tt = tn + off;
+            ti = tt;
+            for (int a = 0; a < 3; ++a) xs[3 * i + a] = fmaf(ti, d[a], o[a]);
+        }
+        if (i > 0) {
+            volatile float dl = ti - tprev;
+            del[i - 1] = (double)dl;
+        }
+        tprev = ti;
+    }
+    return 1;
+}
+
 /* Render R rays through a density grid (order od, 1 channel, sigma =
  * softplus(f), Eq. 9) and a colour grid (order oc, 3 channels, c =
- * sigmoid(f)), both res^3, with S stratified samples per ray:
- *   t_i = near + (i + xi_i) (far - near) / S, xi_i = U(seed, ray_base + r, i),
- *   delta_i = t_{i+1} - t_i (t_S = far),
+ * sigmoid(f)), both res^3, with S stratified samples per ray at the
+ * positions of ray_samples_f32 (xi_i = U(seed, ray_base + r, i)):
  *   C = sum_i T_i (1 - exp(-sigma_i delta_i)) c_i + T_S * bg           (Eq. 10)
  * A ray that misses the cube renders bg. If `target` is given, the loss
  * (1/R) sum_r ||C_r - target_r||^2 (Eq. 11) is returned in *loss and its
@@ -757,11 +798,15 @@ TGO_API int tgo_ray_box(const double *o, const double *d, double *near_, double 
  * two grids). The per-sample derivatives are taken term by term from Eq. 10:
  *   dC/dc_i     = T_i alpha_i
  *   dC/dsigma_i = delta_i T_{i+1} c_i - delta_i (sum_{j>i} T_j alpha_j c_j + T_S bg)
- */
+ * dabs / cabs (optional) accumulate, per coefficient, the magnitude of the
+ * terms of its gradient that FP32 rounding acts on: every difference above
+ * (C - target, and the two parts of dC/dsigma_i) taken with both parts
+ * positive, times |w_i phi_k| of the query's Jacobian. */
 TGO_API void tgo_render(int res, int od, const double *dcoef, int oc, const double *ccoef,
                         int64_t R, int S, const float *rays_o, const float *rays_d,
                         uint64_t seed, uint64_t ray_base, double bg, double *rgb_out,
-                        const float *target, double *dgrad, double *cgrad, double *loss)
+                        const float *target, double *dgrad, double *cgrad, double *loss,
+                        double *dabs, double *cabs)
 {
     double total = 0.0;
     double *sig = (double *)malloc(sizeof(double) * S);
@@ -769,22 +814,14 @@ TGO_API void tgo_render(int res, int od, const double *dcoef, int oc, const doub
     double *col = (double *)malloc(sizeof(double) * S * 3);
     double *del = (double *)malloc(sizeof(double) * S);
     double *Tr = (double *)malloc(sizeof(double) * (S + 1));
+    double *rest = (double *)malloc(sizeof(double) * (S + 1) * 3);
     float *xs = (float *)malloc(sizeof(float) * S * 3);
+    const int64_t nd = (int64_t)res * res * res * tgo_num_coefs(3, od), nc = (int64_t)res * res * res * 3 * tgo_num_coefs(3, oc);
+    double *scratch = (dabs || cabs) ? (double *)calloc((size_t)(nd > nc ? nd : nc), sizeof(double)) : NULL;
     for (int64_t r = 0; r < R; ++r) {
-        double o[3], d[3], nr, fr;
-        for (int a = 0; a < 3; ++a) { o[a] = rays_o[3 * r + a]; d[a] = rays_d[3 * r + a]; }
         double C[3] = {bg, bg, bg};
-        int hit = tgo_ray_box(o, d, &nr, &fr);
+        int hit = ray_samples_f32(rays_o + 3 * r, rays_d + 3 * r, S, seed, ray_base + (uint64_t)r, xs, del);
         if (hit) {
-            double ts_next = 0;
-            for (int i = 0; i < S; ++i) {
-                double xi = tgo_uniform(seed, ray_base + (uint64_t)r, (uint64_t)i);
-                double ti = nr + ((double)i + xi) * (fr - nr) / (double)S;
-                double xi1 = i + 1 < S ? tgo_uniform(seed, ray_base + (uint64_t)r, (uint64_t)(i + 1)) : 0;
-                ts_next = i + 1 < S ? nr + ((double)(i + 1) + xi1) * (fr - nr) / (double)S : fr;
-                del[i] = ts_next - ti;
-                for (int a = 0; a < 3; ++a) xs[3 * i + a] = (float)(o[a] + ti * d[a]);
-            }
             double fc[3];
             for (int i = 0; i < S; ++i) {
                 double fd;
@@ -808,23 +845,37 @@ TGO_API void tgo_render(int res, int od, const double *dcoef, int oc, const doub
                 C[a] = c + Tr[S] * bg;
             }
             if (target) {
-                double g[3];
-                for (int a = 0; a < 3; ++a) g[a] = 2.0 * (C[a] - (double)target[3 * r + a]) / (double)R;
+                double g[3], gs[3];
+                for (int a = 0; a < 3; ++a) {
+                    g[a] = 2.0 * (C[a] - (double)target[3 * r + a]) / (double)R;
+                    gs[a] = 2.0 * (fabs(C[a]) + fabs((double)target[3 * r + a])) / (double)R;
+                }
+                for (int a = 0; a < 3; ++a) {      /* rest_i = sum_{j>i} T_j alpha_j c_j + T_S bg */
+                    rest[3 * S + a] = Tr[S] * bg;
+                    for (int i = S - 1; i >= 0; --i)
+                        rest[3 * i + a] = rest[3 * (i + 1) + a] + Tr[i] * (1.0 - exp(-sig[i] * del[i])) * col[3 * i + a];
+                }
                 for (int i = 0; i < S; ++i) {
                     double alpha = 1.0 - exp(-sig[i] * del[i]);
-                    double dsig = 0, dcol[3];
+                    double dsig = 0, dsig_s = 0, dcol[3], dcol_s[3];
                     for (int a = 0; a < 3; ++a) {
-                        double rest = Tr[S] * bg;
-                        for (int j = i + 1; j < S; ++j) rest += Tr[j] * (1.0 - exp(-sig[j] * del[j])) * col[3 * j + a];
-                        dsig += g[a] * (del[i] * Tr[i + 1] * col[3 * i + a] - del[i] * rest);
+                        const double behind = rest[3 * (i + 1) + a];
+                        dsig += g[a] * (del[i] * Tr[i + 1] * col[3 * i + a] - del[i] * behind);
+                        dsig_s += gs[a] * del[i] * (Tr[i + 1] * col[3 * i + a] + behind);
                         dcol[a] = g[a] * Tr[i] * alpha;
+                        dcol_s[a] = gs[a] * Tr[i] * alpha;
                     }
                     /* chain through sigma = softplus(f) and c = sigmoid(f) into Eq. 3/4 */
-                    double dfd = dsig * sigmoid(fs[i]);
-                    double dfc[3];
-                    for (int a = 0; a < 3; ++a) dfc[a] = dcol[a] * col[3 * i + a] * (1.0 - col[3 * i + a]);
+                    double dfd = dsig * sigmoid(fs[i]), dfd_s = dsig_s * sigmoid(fs[i]);
+                    double dfc[3], dfc_s[3];
+                    for (int a = 0; a < 3; ++a) {
+                        dfc[a] = dcol[a] * col[3 * i + a] * (1.0 - col[3 * i + a]);
+                        dfc_s[a] = dcol_s[a] * col[3 * i + a] * (1.0 - col[3 * i + a]);
+                    }
                     tgo_query_backward(3, res, od, 1, 1, xs + 3 * i, &dfd, NULL, dgrad, NULL);
                     tgo_query_backward(3, res, oc, 3, 1, xs + 3 * i, dfc, NULL, cgrad, NULL);
+                    if (dabs) tgo_query_backward(3, res, od, 1, 1, xs + 3 * i, &dfd_s, NULL, scratch, dabs);
+                    if (cabs) tgo_query_backward(3, res, oc, 3, 1, xs + 3 * i, dfc_s, NULL, scratch, cabs);
                 }
             }
         }
@@ -833,7 +884,7 @@ TGO_API void tgo_render(int res, int od, const double *dcoef, int oc, const doub
             for (int a = 0; a < 3; ++a) total += (C[a] - (double)target[3 * r + a]) * (C[a] - (double)target[3 * r + a]);
     }
     if (loss) *loss = total / (double)R;
-    free(sig); free(fs); free(col); free(del); free(Tr); free(xs);
+    free(sig); free(fs); free(col); free(del); free(Tr); free(rest); free(xs); free(scratch);
 }
 
 /* Ground truth of the synthetic radiance scene (stand-in for Synthetic-NeRF,

@@ -54,7 +54,7 @@ __device__ __forceinline__ bool ray_box(const float *o, const float *d, float &t
             if (o[a] < 0.f || o[a] > 1.f) return false;
             continue;
         }
-        float t0 = (0.f - o[a]) / d[a], t1 = (1.f - o[a]) / d[a];
+        float t0 = __fdiv_rn(0.f - o[a], d[a]), t1 = __fdiv_rn(1.f - o[a], d[a]);
         if (t0 > t1) { float s = t0; t0 = t1; t1 = s; }
         tn = fmaxf(tn, t0);
         tf = fminf(tf, t1);
@@ -73,6 +73,21 @@ __device__ __forceinline__ float warp_excl_scan(float v, float &total)
     }
     total = __shfl_sync(0xffffffffu, incl, 31);
     return incl - v;
+}
+
+// Sum of v over the lanes above this one (0 on lane 31): an inclusive suffix
+// scan by shuffles down, then shifted by one lane.
+__device__ __forceinline__ float warp_excl_suffix(float v)
+{
+    const int lane = threadIdx.x & 31;
+    float incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float u = __shfl_down_sync(0xffffffffu, incl, o);
+        if (lane + o < 32) incl += u;
+    }
+    const float ex = __shfl_down_sync(0xffffffffu, incl, 1);
+    return lane == 31 ? 0.f : ex;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -98,7 +113,8 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
         float tn, tf;
         const bool hit = ray_box(o, d, tn, tf);
         const uint64_t key = stream_key(seed, ray_base + (uint64_t)r);
-        const float step = hit ? (tf - tn) / (float)S : 0.f;
+        // sample positions by the FP32 rule t_i = tn + (i + xi_i) step, every operation rounded once
+        const float step = hit ? __fdiv_rn(__fsub_rn(tf, tn), (float)S) : 0.f;
         // per-lane samples: optical depth tau = sigma delta, colour, raw field values
         float tau[kMaxSamplesPerLane], col[kMaxSamplesPerLane][3], fd[kMaxSamplesPerLane], dlt[kMaxSamplesPerLane];
         float xsmp[kMaxSamplesPerLane][3];
@@ -112,8 +128,10 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
             col[k][0] = col[k][1] = col[k][2] = 0.f;
             xsmp[k][0] = xsmp[k][1] = xsmp[k][2] = 0.f;
             if (k < m && i < S && hit) {
-                const float ti = tn + ((float)i + uniform_k(key, (uint64_t)i)) * step;
-                const float tnext = (i + 1 < S) ? tn + ((float)(i + 1) + uniform_k(key, (uint64_t)(i + 1))) * step : tf;
+                const float ti = __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, uniform_k(key, (uint64_t)i)), step));
+                const float tnext =
+                    (i + 1 < S) ? __fadd_rn(tn, __fmul_rn(__fadd_rn((float)(i + 1), uniform_k(key, (uint64_t)(i + 1))), step))
+                                : tf;
                 const float x[3] = {fmaf(ti, d[0], o[0]), fmaf(ti, d[1], o[1]), fmaf(ti, d[2], o[2])};
                 float fc[3];
                 field_value<TD, OD, 1>(dcoef, res, x, &fd[k]);
@@ -136,7 +154,7 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
 #pragma unroll
         for (int k = 0; k < kMaxSamplesPerLane; ++k) {
             Ti[k] = expf(-run);
-            const float wgt = Ti[k] * (1.f - expf(-tau[k]));
+            const float wgt = Ti[k] * -expm1f(-tau[k]);       // T_i alpha_i, alpha_i without the 1 - exp cancellation
 #pragma unroll
             for (int a = 0; a < 3; ++a) acc[a] = fmaf(wgt, col[k][a], acc[a]);
             run += tau[k];
@@ -162,28 +180,25 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
             }
         }
         if (target && lane == 0) atomicAdd(loss, l);
-        // P_i = sum_{j<=i} T_j alpha_j c_j: lane-exclusive prefix + in-lane running sum
-        float pre[3];
+        // behind_i = sum_{j>i} T_j alpha_j c_j + T_S bg, formed as a suffix sum (the lanes above this one,
+        // then this lane's samples from the last one down) so it is never a difference of two sums
+        float behind[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float tot;
-            pre[a] = warp_excl_scan(acc[a], tot);
-        }
+        for (int a = 0; a < 3; ++a) behind[a] = warp_excl_suffix(acc[a]) + T_end * bg;
 #pragma unroll
-        for (int k = 0; k < kMaxSamplesPerLane; ++k) {
+        for (int k = kMaxSamplesPerLane - 1; k >= 0; --k) {
             const int i = lane * m + k;
             if (!(k < m && i < S)) continue;
-            const float alpha = 1.f - expf(-tau[k]);
-            const float Tn = Ti[k] * (1.f - alpha);              // T_{i+1}
+            const float alpha = -expm1f(-tau[k]);
+            const float Tn = Ti[k] * expf(-tau[k]);              // T_{i+1}
             const float delta_i = dlt[k];
             float dsig = 0.f, dfc[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const float w = Ti[k] * alpha * col[k][a];
-                pre[a] += w;                                     // now P_i (inclusive)
-                const float rest = Cr[a] - pre[a];               // sum_{j>i} T_j alpha_j c_j + T_S bg
-                dsig = fmaf(g[a], delta_i * (Tn * col[k][a] - rest), dsig);
+                dsig = fmaf(g[a], delta_i * (Tn * col[k][a] - behind[a]), dsig);
                 dfc[a] = g[a] * Ti[k] * alpha * col[k][a] * (1.f - col[k][a]);
+                behind[a] += w;                                  // sample i is behind sample i - 1
             }
             const int64_t sidx = r * S + i;
             if (hit) {

@@ -571,10 +571,11 @@ def test_render_homogeneous_closed_form():
             np.testing.assert_allclose(rgb[r], [1, 1, 1]); continue
         # stratified samples: delta_i = t_{i+1} - t_i with t_S = far, so the
         # optical depth covers [t_0, far], t_0 = near + xi_0 (far - near) / S
+        # (the oracle places samples by the FP32 rule, so t_0 and far carry FP32 rounding: rtol 1e-6)
         t0 = n + float(W.uniform(3, r, 0)) * (f - n) / 64
         T = math.exp(-sigma * (f - t0))
         want = [sg(c) * (1 - T) + T for c in (g0, 0.1, 0.9)]
-        np.testing.assert_allclose(rgb[r], want, rtol=1e-12)
+        np.testing.assert_allclose(rgb[r], want, rtol=1e-6)
     assert not oracle.ray_box(o[2].astype(np.float64), d[2].astype(np.float64))[0]
 
 
