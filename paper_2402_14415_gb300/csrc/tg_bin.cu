@@ -525,7 +525,7 @@ tg_status ensure_stage(tg_batch *bt, int64_t floats, const char *who)
         return fail(TG_EINVAL, "%s: the request needs %lld staging floats, the fixed scratch holds %lld", who,
                     (long long)floats, (long long)bt->stage_floats);
     float *p = nullptr;
-    tg_status st = cuda_status(cudaMalloc(&p, (size_t)floats * sizeof(float)), who);
+    tg_status st = dev_alloc((void **)&p, (size_t)floats * sizeof(float), who);
     if (st != TG_OK) return st;
     if (bt->stage) {
         cudaDeviceSynchronize();
@@ -541,7 +541,7 @@ tg_status ensure_aux(tg_batch *bt, int64_t floats, const char *who)
 {
     if (bt->aux_floats >= floats) return TG_OK;
     float *p = nullptr;
-    tg_status st = cuda_status(cudaMalloc(&p, (size_t)floats * sizeof(float)), who);
+    tg_status st = dev_alloc((void **)&p, (size_t)floats * sizeof(float), who);
     if (st != TG_OK) return st;
     if (bt->aux) {
         cudaDeviceSynchronize();
@@ -597,17 +597,17 @@ tg_status tg_batch_create(int dim, int res, int64_t max_points, tg_batch **out)
         b->nbricks *= b->nb[d];
     }
     b->G = b->nbricks <= kMaxSmemBins ? kBinChunksPerSm * num_sms() : 0;
-    tg_status st = cuda_status(cudaMalloc(&b->counts, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->offsets, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->cursor, b->nbricks * sizeof(int)), "tg_batch_create");
+    tg_status st = dev_alloc((void **)&b->counts, (b->nbricks + 1) * sizeof(int), "tg_batch_create");
+    if (st == TG_OK) st = dev_alloc((void **)&b->offsets, (b->nbricks + 1) * sizeof(int), "tg_batch_create");
+    if (st == TG_OK) st = dev_alloc((void **)&b->cursor, b->nbricks * sizeof(int), "tg_batch_create");
     if (st == TG_OK && b->G)
-        st = cuda_status(cudaMalloc(&b->hist, (size_t)b->G * b->nbricks * sizeof(int)), "tg_batch_create");
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->sorted, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
+        st = dev_alloc((void **)&b->hist, (size_t)b->G * b->nbricks * sizeof(int), "tg_batch_create");
+    if (st == TG_OK) st = dev_alloc((void **)&b->sorted, (max_points > 0 ? max_points : 1) * sizeof(float4), "tg_batch_create");
     if (st == TG_OK && b->G)
-        st = cuda_status(cudaMalloc(&b->coarse, (max_points > 0 ? max_points : 1) * sizeof(float4)), "tg_batch_create");
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->perm, (max_points > 0 ? max_points : 1) * sizeof(int)), "tg_batch_create");
+        st = dev_alloc((void **)&b->coarse, (max_points > 0 ? max_points : 1) * sizeof(float4), "tg_batch_create");
+    if (st == TG_OK) st = dev_alloc((void **)&b->perm, (max_points > 0 ? max_points : 1) * sizeof(int), "tg_batch_create");
     b->stage_owned = true;        // staging for the fused training steps is allocated on first use
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&b->status, sizeof(int)), "tg_batch_create");
+    if (st == TG_OK) st = dev_alloc((void **)&b->status, sizeof(int), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->offsets, 0, (b->nbricks + 1) * sizeof(int)), "tg_batch_create");
     if (st == TG_OK) st = cuda_status(cudaMemset(b->status, 0, sizeof(int)), "tg_batch_create");
     if (st == TG_OK && b->G) {
@@ -707,12 +707,23 @@ tg_status tg_batch_scatter(const tg_batch *b, const float *src, int width, float
 tg_status tg_batch_timeouts(tg_batch *b, int *timed_out)
 {
     if (!b || !timed_out) return fail(TG_EINVAL, "tg_batch_timeouts: NULL argument");
-    int v = 0;
-    tg_status st = cuda_status(cudaMemcpy(&v, b->status, sizeof(int), cudaMemcpyDeviceToHost), "tg_batch_timeouts");
+    // every stream's launches, non-blocking streams included, have finished before the flag is read
+    tg_status st = cuda_status(cudaDeviceSynchronize(), "tg_batch_timeouts: wait for the device");
     if (st != TG_OK) return st;
+    int v = 0;
+    if ((st = cuda_status(cudaMemcpy(&v, b->status, sizeof(int), cudaMemcpyDeviceToHost), "tg_batch_timeouts")) != TG_OK)
+        return st;
     *timed_out = v;
-    if (v) cudaMemset(b->status, 0, sizeof(int));
-    return TG_OK;
+    if (v) st = cuda_status(cudaMemset(b->status, 0, sizeof(int)), "tg_batch_timeouts: clear");
+    return st;
+}
+
+tg_status tg_grid_timeouts(tg_grid *g, int *timed_out)
+{
+    if (!g || !timed_out) return fail(TG_EINVAL, "tg_grid_timeouts: NULL argument");
+    *timed_out = 0;
+    if (!g->auto_batch) return cuda_status(cudaDeviceSynchronize(), "tg_grid_timeouts: wait for the device");
+    return tg_batch_timeouts(g->auto_batch, timed_out);
 }
 
 }  // extern "C"

@@ -2,7 +2,9 @@
 // allocate device memory. All of its scratch (brick counters, offsets, write
 // cursors, the sorted point records, the permutation and a status word) lives
 // in one file-scope device array of fixed size; the call itself never
-// allocates.
+// allocates. tg_noalloc_timeouts reads and clears the status word.
+#include <stddef.h>
+
 #include <mutex>
 
 #include "tg_binned.cuh"
@@ -20,6 +22,16 @@ struct NoallocScratch {      // every array starts on a 16-byte boundary
     float4 sorted[kNoallocMaxPoints];
     int perm[kNoallocMaxPoints];
 };
+
+// The vector paths of the scans and the float4 records need every array on a
+// 16-byte boundary (a misaligned layout once raised a misaligned-address fault).
+static_assert(kNoallocMaxBricks % 4 == 0 && kNoallocMaxPoints % 4 == 0, "array sizes must keep 16-byte alignment");
+static_assert(offsetof(NoallocScratch, counts) % 16 == 0, "counts");
+static_assert(offsetof(NoallocScratch, offsets) % 16 == 0, "offsets");
+static_assert(offsetof(NoallocScratch, cursor) % 16 == 0, "cursor");
+static_assert(offsetof(NoallocScratch, status) % 16 == 0, "status");
+static_assert(offsetof(NoallocScratch, sorted) % 16 == 0, "sorted");
+static_assert(offsetof(NoallocScratch, perm) % 16 == 0, "perm");
 
 // About 5.6 MB; every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
@@ -60,6 +72,12 @@ extern "C" tg_status tg_query_noalloc(const tg_grid *g, const float *pts, int64_
                     (long long)N, (long long)kNoallocMaxPoints);
     if (N == 0) return TG_OK;
     if (!pts || !out) return fail(TG_EINVAL, "tg_query_noalloc: NULL pts or out");
+    int dev = -1;
+    tg_status st = cuda_status(cudaGetDevice(&dev), "tg_query_noalloc: cudaGetDevice");
+    if (st != TG_OK) return st;
+    if (dev != g->device)     // the scratch and the coefficients must be on one GPU
+        return fail(TG_EINVAL, "tg_query_noalloc: the grid lives on device %d but device %d is current", g->device,
+                    dev);
     tg_batch b = {};
     b.dim = 3;
     b.res = g->res;
@@ -72,7 +90,7 @@ extern "C" tg_status tg_query_noalloc(const tg_grid *g, const float *pts, int64_
         return fail(TG_EINVAL, "tg_query_noalloc: res = %d needs %lld bricks, over the fixed limit of %lld",
                     g->res, (long long)b.nbricks, (long long)kNoallocMaxBricks);
     NoallocScratch *s = nullptr;
-    tg_status st = scratch_address(&s);
+    st = scratch_address(&s);
     if (st != TG_OK) return st;
     b.max_points = kNoallocMaxPoints;
     b.G = 0;                       // global-atomic binning: needs no per-chunk histogram
@@ -86,10 +104,24 @@ extern "C" tg_status tg_query_noalloc(const tg_grid *g, const float *pts, int64_
     b.stage_floats = 0;
     b.stage_owned = false;
     b.status = s->status;
-    cudaGetDevice(&b.device);
-    st = cuda_status(cudaMemsetAsync(s->status, 0, sizeof(int), (cudaStream_t)stream), "tg_query_noalloc: clear status");
-    if (st != TG_OK) return st;
+    b.device = dev;
     st = tg_batch_bin(&b, pts, N, stream);     // clears the brick counters before counting
     if (st != TG_OK) return st;
     return tg_query_binned(g, &b, out, grad_x, TG_ORDER_INPUT, stream);
+}
+
+extern "C" tg_status tg_noalloc_timeouts(int *timed_out)
+{
+    if (!timed_out) return fail(TG_EINVAL, "tg_noalloc_timeouts: timed_out is NULL");
+    NoallocScratch *s = nullptr;
+    tg_status st = scratch_address(&s);
+    if (st != TG_OK) return st;
+    if ((st = cuda_status(cudaDeviceSynchronize(), "tg_noalloc_timeouts: wait for the device")) != TG_OK) return st;
+    int v = 0;
+    if ((st = cuda_status(cudaMemcpy(&v, s->status, sizeof(int), cudaMemcpyDeviceToHost), "tg_noalloc_timeouts")) !=
+        TG_OK)
+        return st;
+    *timed_out = v;
+    if (v) st = cuda_status(cudaMemset(s->status, 0, sizeof(int)), "tg_noalloc_timeouts: clear");
+    return st;
 }
