@@ -75,6 +75,14 @@ TG_API const char *tg_status_string(tg_status s);
 /* Description of the last failure on the calling thread (static, per thread). */
 TG_API const char *tg_last_error(void);
 
+/* Host-side fault injection for tests of the failure paths (no paper
+ * counterpart): after this call the next `pass` device allocations made by
+ * the library succeed and the `fail` allocations after them report TG_ENOMEM
+ * without reaching the CUDA allocator; fail = 0 switches injection off.
+ * Process-wide. The GPU never sees a fault: the failing call returns
+ * TG_ENOMEM and frees what it had allocated. Errors: TG_EINVAL (negative). */
+TG_API tg_status tg_inject_alloc_failures(int pass, int fail);
+
 /* ---------------------------------------------------------------------------
  * Grid storage V_T (Sec. 3.1: "a dense grid G of size w x d x h", each vertex
  * storing the low-order Taylor series).
@@ -258,10 +266,15 @@ TG_API tg_status tg_batch_gather(const tg_batch *batch, const float *src, int wi
 TG_API tg_status tg_batch_scatter(const tg_batch *batch, const float *src, int width, float *dst, tg_stream stream);
 
 /* The binned kernels wait on their TMA copies with a 2 s limit; a wait that
- * gives up sets a device flag instead of hanging. Synchronously reads that
- * flag into *timed_out (non-zero = some launch since the last call gave up,
- * its outputs are invalid) and clears it. */
+ * gives up sets a device flag instead of hanging. Waits for all work on the
+ * current device (cudaDeviceSynchronize), then reads that flag into
+ * *timed_out (non-zero = some launch on this batch since the last call gave
+ * up, its outputs are invalid) and clears it. Not for use during capture. */
 TG_API tg_status tg_batch_timeouts(tg_batch *batch, int *timed_out);
+
+/* The same for the batch that tg_query / tg_query_backward bin large 3-D
+ * batches into (owned by the grid): *timed_out = 0 when no call has binned. */
+TG_API tg_status tg_grid_timeouts(tg_grid *grid, int *timed_out);
 
 /* Binned forward query that allocates nothing (the paper has no counterpart;
  * this is a deployment convenience). Some callers cannot call cudaMalloc:
@@ -274,6 +287,9 @@ TG_API tg_status tg_batch_timeouts(tg_batch *batch, int *timed_out);
  * library keeps it until the process exits).
  * Limits: N <= 262144 points and res <= 257 (at most 32768 bricks); other
  * requests fail with TG_EINVAL and a message. 3-D grids only, with the same shape rules as tg_query_binned.
+ * The grid's device must be the current device (TG_EINVAL otherwise).
+ * A TMA wait that gives up is reported by tg_noalloc_timeouts, not by the
+ * return status of this call (which only enqueues).
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.
  * Every call reuses the same array and leaves its contents behind (the call
@@ -281,6 +297,13 @@ TG_API tg_status tg_batch_timeouts(tg_batch *batch, int *timed_out);
  * streams, or from two threads - race and give wrong results: serialise them. */
 TG_API tg_status tg_query_noalloc(const tg_grid *grid, const float *pts, int64_t N,
                                   float *out, float *grad_x, tg_stream stream);
+
+/* Timeout report of tg_query_noalloc (allocates nothing either): waits for
+ * all work on the current device, reads the fixed array's status word into
+ * *timed_out (non-zero = a bounded TMA wait of some call on this device gave
+ * up since the last read, and that call's outputs are invalid) and clears it.
+ * Errors: TG_EINVAL (NULL), TG_EDEVICE. */
+TG_API tg_status tg_noalloc_timeouts(int *timed_out);
 
 /* ---------------------------------------------------------------------------
  * Optimiser. The paper fixes only the learning rate (Sec. 4.1, "fixed

@@ -84,6 +84,9 @@ _SIGS = {
     "tg_batch_order": [_vp, _vp, _vp],
     "tg_batch_points": [_vp, _vp, _vp],
     "tg_batch_timeouts": [_vp, ctypes.POINTER(_int)],
+    "tg_grid_timeouts": [_vp, ctypes.POINTER(_int)],
+    "tg_inject_alloc_failures": [_int, _int],
+    "tg_noalloc_timeouts": [ctypes.POINTER(_int)],
     "tg_batch_gather": [_vp, _vp, _int, _vp, _vp],
     "tg_batch_scatter": [_vp, _vp, _int, _vp, _vp],
     "tg_query_noalloc": [_vp, _vp, _i64, _vp, _vp, _vp],
@@ -352,6 +355,26 @@ def tg_batch_scatter(batch: Batch, src: torch.Tensor, dst=None, stream=None) -> 
 def tg_batch_timeouts(batch: Batch) -> int:
     v = _int(0)
     _check(load().tg_batch_timeouts(batch.handle, ctypes.byref(v)), "tg_batch_timeouts")
+    return v.value
+
+
+def tg_inject_alloc_failures(pass_: int, fail: int) -> None:
+    """Test hook: the next `pass_` device allocations of the library succeed, the `fail` after them report
+    TG_ENOMEM (host-side; no GPU fault). fail = 0 switches injection off."""
+    _check(load().tg_inject_alloc_failures(int(pass_), int(fail)), "tg_inject_alloc_failures")
+
+
+def tg_grid_timeouts(grid: Grid) -> int:
+    """Non-zero if a bounded TMA wait of a binned call made by tg_query / tg_query_backward gave up (clears it)."""
+    v = _int(0)
+    _check(load().tg_grid_timeouts(grid.handle, ctypes.byref(v)), "tg_grid_timeouts")
+    return v.value
+
+
+def tg_noalloc_timeouts() -> int:
+    """Non-zero if a bounded TMA wait of a tg_query_noalloc call on the current device gave up (clears it)."""
+    v = _int(0)
+    _check(load().tg_noalloc_timeouts(ctypes.byref(v)), "tg_noalloc_timeouts")
     return v.value
 
 

@@ -109,8 +109,8 @@ namespace tg {
 tg_status ensure_adam_state(tg_grid *g)
 {
     if (g->adam_m) return TG_OK;
-    tg_status st = cuda_status(cudaMalloc(&g->adam_m, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(m)");
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&g->adam_v, (size_t)g->ncoef * 4 + 16), "tg_adam_step: cudaMalloc(v)");
+    tg_status st = dev_alloc((void **)&g->adam_m, (size_t)g->ncoef * 4 + 16, "tg_adam_step: cudaMalloc(m)");
+    if (st == TG_OK) st = dev_alloc((void **)&g->adam_v, (size_t)g->ncoef * 4 + 16, "tg_adam_step: cudaMalloc(v)");
     if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_m, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero m");
     if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_v, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero v");
     if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_adam_step: init moments");

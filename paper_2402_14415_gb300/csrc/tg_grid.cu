@@ -1,4 +1,5 @@
 // Grid storage V_T (Sec. 3.1): creation, coefficient exchange, status strings.
+#include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -34,6 +35,32 @@ tg_status cuda_status(cudaError_t e, const char *what)
 }
 
 tg_status launch_status(const char *what) { return cuda_status(cudaGetLastError(), what); }
+
+// Failure injection (tg_inject_alloc_failures): the next g_alloc_pass
+// allocations go through, the g_alloc_fail after them report TG_ENOMEM.
+static std::atomic<int> g_alloc_pass{0}, g_alloc_fail{0};
+
+static bool injected_failure()
+{
+    if (g_alloc_fail.load() <= 0) return false;
+    if (g_alloc_pass.fetch_sub(1) > 0) return false;
+    g_alloc_pass.store(0);
+    return g_alloc_fail.fetch_sub(1) > 0;
+}
+
+tg_status dev_alloc(void **p, size_t bytes, const char *what)
+{
+    *p = nullptr;
+    if (injected_failure()) return fail(TG_ENOMEM, "%s: allocation of %zu bytes failed (injected)", what, bytes);
+    return cuda_status(cudaMalloc(p, bytes), what);
+}
+
+tg_status dev_alloc_async(void **p, size_t bytes, cudaStream_t s, const char *what)
+{
+    *p = nullptr;
+    if (injected_failure()) return fail(TG_ENOMEM, "%s: allocation of %zu bytes failed (injected)", what, bytes);
+    return cuda_status(cudaMallocAsync(p, bytes, s), what);
+}
 
 int num_sms()
 {
@@ -109,6 +136,15 @@ using namespace tg;
 
 extern "C" {
 
+tg_status tg_inject_alloc_failures(int pass, int fail_count)
+{
+    if (pass < 0 || fail_count < 0) return fail(TG_EINVAL, "tg_inject_alloc_failures: negative count");
+    g_alloc_fail.store(0);
+    g_alloc_pass.store(pass);
+    g_alloc_fail.store(fail_count);
+    return TG_OK;
+}
+
 const char *tg_status_string(tg_status s)
 {
     switch (s) {
@@ -147,10 +183,10 @@ tg_status tg_create(int dim, int res, int order, int channels, tg_dtype dtype, u
     g->ncoef = g->nv * channels * g->K;
     cudaGetDevice(&g->device);
 
-    tg_status st = cuda_status(cudaMalloc(&g->master, (size_t)g->ncoef * 4 + 16), "tg_create: cudaMalloc(master)");
+    tg_status st = dev_alloc((void **)&g->master, (size_t)g->ncoef * 4 + 16, "tg_create: cudaMalloc(master)");
     if (st == TG_OK) {
         if (dtype == TG_F32) g->store = g->master;
-        else st = cuda_status(cudaMalloc(&g->store, (size_t)g->ncoef * 2 + 16), "tg_create: cudaMalloc(store)");
+        else st = dev_alloc((void **)&g->store, (size_t)g->ncoef * 2 + 16, "tg_create: cudaMalloc(store)");
     }
     if (st == TG_OK) {
         uint64_t key = 0;

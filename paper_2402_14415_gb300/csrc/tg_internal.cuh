@@ -33,6 +33,12 @@ tg_status cuda_status(cudaError_t e, const char *what);
 // Checks the launch error of the previous kernel.
 tg_status launch_status(const char *what);
 
+// Every device allocation of the library goes through these two: cudaMalloc /
+// cudaMallocAsync with the status mapped (TG_ENOMEM when the device is out of
+// memory), after the failure-injection counter of tg_inject_alloc_failures.
+tg_status dev_alloc(void **p, size_t bytes, const char *what);
+tg_status dev_alloc_async(void **p, size_t bytes, cudaStream_t s, const char *what);
+
 int num_sms();                      // SM count of the current device (cached per device)
 constexpr int kBinChunksPerSm = 1;  // point chunks of the binning per SM (one histogram row each; 2 measured slower)
 // Resident blocks per SM of a kernel at a launch shape (cached per device and kernel).

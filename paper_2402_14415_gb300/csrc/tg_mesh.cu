@@ -411,11 +411,11 @@ extern "C" tg_status tg_extract_mesh(const tg_grid *g, int M, float iso, float *
     float *vals = nullptr;
     int *row_count = nullptr;
     int64_t *row_off = nullptr;
-    tg_status st = cuda_status(cudaMallocAsync((void **)&vals, nl * sizeof(float), s), "tg_extract_mesh: lattice");
+    tg_status st = dev_alloc_async((void **)&vals, nl * sizeof(float), s, "tg_extract_mesh: lattice");
     if (st == TG_OK)
-        st = cuda_status(cudaMallocAsync((void **)&row_count, rows * sizeof(int), s), "tg_extract_mesh: counts");
+        st = dev_alloc_async((void **)&row_count, rows * sizeof(int), s, "tg_extract_mesh: counts");
     if (st == TG_OK)
-        st = cuda_status(cudaMallocAsync((void **)&row_off, rows * sizeof(int64_t), s), "tg_extract_mesh: offsets");
+        st = dev_alloc_async((void **)&row_off, rows * sizeof(int64_t), s, "tg_extract_mesh: offsets");
     if (st == TG_OK) {
 #define TG_LAT(D, O, C) lattice_dtype<O, C>(g, M, vals, s)
         st = TG_DISPATCH_SHAPE(g->dim, g->order, g->C, TG_LAT);
@@ -449,9 +449,9 @@ extern "C" tg_status tg_sample_mesh(const float *tris, const int64_t *n_tris, in
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t cap = max_tris > 0 ? max_tris : 1;
     double *area = nullptr, *excl = nullptr, *total = nullptr;
-    tg_status st = cuda_status(cudaMallocAsync((void **)&area, cap * sizeof(double), s), "tg_sample_mesh: areas");
-    if (st == TG_OK) st = cuda_status(cudaMallocAsync((void **)&excl, cap * sizeof(double), s), "tg_sample_mesh: scan");
-    if (st == TG_OK) st = cuda_status(cudaMallocAsync((void **)&total, sizeof(double), s), "tg_sample_mesh: total");
+    tg_status st = dev_alloc_async((void **)&area, cap * sizeof(double), s, "tg_sample_mesh: areas");
+    if (st == TG_OK) st = dev_alloc_async((void **)&excl, cap * sizeof(double), s, "tg_sample_mesh: scan");
+    if (st == TG_OK) st = dev_alloc_async((void **)&total, sizeof(double), s, "tg_sample_mesh: total");
     if (st == TG_OK && max_tris > 0) {
         const int64_t need = (max_tris + kMeshThreads - 1) / kMeshThreads, lim = (int64_t)num_sms() * 16;
         tri_area_kernel<<<(unsigned)(need < lim ? need : lim), kMeshThreads, 0, s>>>(tris, n_tris, max_tris, area);

@@ -156,11 +156,11 @@ static tg_status admit_fit(Job *j)
     if (st == TG_OK) st = tg_batch_create(3, d.res, d.points_per_step, &j->batch);
     if (st == TG_OK) st = ensure_stage(j->batch, 11 * d.points_per_step, "server: staging");
     if (st == TG_OK) st = ensure_adam_state(j->grid);
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->grad, (size_t)j->grid->ncoef * 4 + 16), "server: gradient");
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->small, 64), "server: status block");
+    if (st == TG_OK) st = dev_alloc((void **)&j->grad, (size_t)j->grid->ncoef * 4 + 16, "server: gradient");
+    if (st == TG_OK) st = dev_alloc((void **)&j->small, 64, "server: status block");
     const size_t nsh = j->sph.size() + j->box.size() + j->cdf.size();
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->shape_dev, nsh * 4), "server: shape");
-    if (st == TG_OK) st = cuda_status(cudaMalloc(&j->eval_pts, (size_t)d.eval_points * 12), "server: eval points");
+    if (st == TG_OK) st = dev_alloc((void **)&j->shape_dev, nsh * 4, "server: shape");
+    if (st == TG_OK) st = dev_alloc((void **)&j->eval_pts, (size_t)d.eval_points * 12, "server: eval points");
     if (st != TG_OK) return st;
     cudaStream_t s = j->stream;
     st = cuda_status(cudaMemsetAsync(j->grad, 0, (size_t)j->grid->ncoef * 4, s), "server: zero gradient");
