@@ -154,41 +154,77 @@ def replica_seeds(rank: int):
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(n_points: int, coefs64=None):
+def oracle_sample(n_points: int, coefs64):
+    """One fwd+bwd of the oracle on n_points of the workload's points (seed 1) and upstream (seed 4)."""
     import oracle
     import workloads as W
-    if coefs64 is None:   # values do not matter for timing; a fast generator keeps set-up short
-        coefs64 = np.random.default_rng(0).standard_normal(RES ** 3 * C * K)
     pts = W.uniform_points(1, n_points)
     up = W.normal(4, W.STREAM_UPSTREAM, np.arange(n_points, dtype=np.uint64)).reshape(-1, 1)
     t0 = time.perf_counter()
     oracle.query(3, RES, ORDER, C, coefs64, pts, want_grad=False)
     oracle.query_backward(3, RES, ORDER, C, pts, up)
-    return time.perf_counter() - t0, coefs64
+    return time.perf_counter() - t0
+
+
+def host_grid_fp64():
+    """A 256^3 order-2 grid of N(0,1) coefficients for the reference arm, which runs without a GPU. The oracle's
+    arithmetic does not depend on the values, so numpy's generator stands in for the device's (its values
+    differ from the GPU grid's; the main line's baseline runs on the GPU grid's own coefficients)."""
+    return np.random.default_rng(0).standard_normal(RES ** 3 * C * K)
 
 
 def threads_used() -> int:
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    """OpenMP threads of the oracle: OMP_NUM_THREADS if set, else every core this process may run on (nproc)."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    env = os.environ.get("OMP_NUM_THREADS")
+    return min(int(env), n) if env else n
+
+
+def oracle_rate(coefs64, steps: int, warmup: int, sample: int = CPU_SAMPLE):
+    """Steady-state oracle throughput: `warmup` untimed samples of sample / 16 points, then `steps` timed samples."""
+    for _ in range(warmup):
+        oracle_sample(sample // 16, coefs64)
+    total = sum(oracle_sample(sample, coefs64) for _ in range(steps))
+    return sample * steps / total / 1e6, total
+
+
+def cpu_baseline_of(coefs32, steps: int = 5, warmup: int = 3):
+    """The oracle timed on the given grid in a fresh process (no CUDA context, no torch thread pool beside the
+    oracle's OpenMP threads), on `steps` samples of CPU_SAMPLE points after `warmup` smaller untimed ones."""
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    try:
+        np.save(path, coefs32)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-from", path,
+                            "--steps", str(steps), "--warmup", str(warmup)], capture_output=True, text=True,
+                           check=True)
+    finally:
+        os.unlink(path)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_cpu_baseline(path: str, steps: int, warmup: int):
+    coefs64 = np.load(path).astype(np.float64)
+    value, _ = oracle_rate(coefs64, steps, warmup)
+    print(json.dumps({"value": value, "unit": "Mpts/s", "cores": threads_used(), "kind": "oracle",
+                      "sample": f"{steps} x {CPU_SAMPLE} of the 2^24 points (the first {CPU_SAMPLE} of the "
+                                f"workload's points and upstream) after {warmup} untimed warm-up samples, on the "
+                                "coefficients of the GPU's grid, in a process of its own"}), flush=True)
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    coefs = None
-    for _ in range(args.warmup):
-        _, coefs = oracle_sample(CPU_SAMPLE // 16, coefs)
-    total = 0.0
-    for _ in range(args.steps):
-        dt, coefs = oracle_sample(CPU_SAMPLE, coefs)
-        total += dt
-    value = CPU_SAMPLE * args.steps / total / 1e6
+    value, total = oracle_rate(host_grid_fp64(), args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_points_per_step": CPU_SAMPLE},
         "cpu_baseline": {"value": value, "unit": "Mpts/s", "cores": threads_used(), "kind": "oracle",
-                         "sample": f"{CPU_SAMPLE} of the 2^24 points per step on the same 256^3 order-2 grid"},
+                         "sample": f"{CPU_SAMPLE} of the 2^24 points per step (the first {CPU_SAMPLE} of the "
+                                   "workload's points and upstream), on a 256^3 order-2 grid of N(0,1) coefficients "
+                                   "(numpy's generator: values differ from the GPU grid's, the arithmetic does not)"},
         "e2e": {"value": value, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -335,10 +371,7 @@ def run_ours(args, world, rank, local):
         if not args.no_serving:
             line["configs"]["serving"] = bench_serving()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, _ = oracle_sample(CPU_SAMPLE)
-        line["cpu_baseline"] = {"value": CPU_SAMPLE / dt / 1e6, "unit": "Mpts/s", "cores": threads_used(),
-                                "kind": "oracle",
-                                "sample": f"{CPU_SAMPLE} of the 2^24 points, same 256^3 order-2 grid, one fwd+bwd"}
+        line["cpu_baseline"] = cpu_baseline_of(tg.tg_get_coefs(g).cpu().numpy())      # the very grid the GPU ran on
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -794,7 +827,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run each kernel of the step once, untimed (for ncu captures)")
     ap.add_argument("--profile-points", type=int, default=N_POINTS)
+    ap.add_argument("--cpu-baseline-from", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_baseline_from:
+        return run_cpu_baseline(args.cpu_baseline_from, args.steps, args.warmup)
     args.warmup = max(args.warmup, 3)
     if args.profile:
         return profile_once()
