@@ -9,7 +9,9 @@
 // the global gradient, which also combines the faces neighbouring bricks share.
 // A brick whose points fit one round stores the tile instead of zeroing it
 // and adding to it.
-#include "tg_gather.cuh"
+#include <stdlib.h>
+
+#include "tg_bwd_fast.cuh"
 
 namespace tg {
 
@@ -238,10 +240,32 @@ brick_bwd_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx, int
     }
 }
 
+// TG_BWD_GATHER=1 in the environment selects the vertex-centric gather kernel for value upstreams too
+// (the pair-list kernel's predecessor), for comparisons.
+static bool list_kernel_disabled()
+{
+    static const bool off = [] {
+        const char *e = getenv("TG_BWD_GATHER");
+        return e && e[0] == '1';
+    }();
+    return off;
+}
+
 template <int ORDER, int C, bool HAS_G, bool IN_ORDER>
 static tg_status launch_bwd(const CUtensorMap &map, const tg_grid *g, const tg_batch *bt, const float *uf,
                             const float *ug, bool det, cudaStream_t s)
 {
+    if constexpr (!HAS_G) {
+        if (!det && !list_kernel_disabled()) {   // value upstreams: the descriptor-driven gather
+            auto k = brick_bwd_fast_kernel<ORDER, C, IN_ORDER>;
+            const int smem = FastLayout<ORDER, C>::bytes;
+            tg_status st = set_smem((const void *)k, smem);
+            if (st != TG_OK) return st;
+            k<<<(unsigned)bt->nbricks, kFThreads, smem, s>>>(map, g->res, bt->nb[0], bt->nb[1], bt->sorted,
+                                                             bt->offsets, uf);
+            return launch_status("tg_query_backward_binned");
+        }
+    }
     if (!det) {
         auto k = brick_bwd_kernel<ORDER, C, HAS_G, IN_ORDER, false>;
         const int smem = BwdLayout<ORDER, C, HAS_G, false>::bytes;
