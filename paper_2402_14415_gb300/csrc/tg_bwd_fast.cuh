@@ -5,17 +5,20 @@
 // A round of at most kFCap points of the brick:
 //   1. locates every point and ranks it within its cell (one shared atomic),
 //   2. scans the 512 cell counts in place into cell offsets and stores the
-//      point's record (t, s) at its cell-sorted slot,
+//      point's record (brick-local grid coordinates u - x0, s) at its
+//      cell-sorted slot,
 //   3. packs, per cell row and vertex x-position, (first slot, points of the
-//      cell below x, points of the cell above x) into one word - one thread per
-//      cell row, from the row's nine offsets - so that a vertex finds each of
-//      its four incident cell rows in one load, and counting-sorts the vertices
-//      by load (heavy first) so that the lanes of a warp walk lists of nearly
-//      equal length,
+//      two cells beside x) into one word - one thread per cell row, from the
+//      row's nine offsets - so that a vertex finds each of its four incident
+//      cell rows in one load, and counting-sorts the vertices by load (heavy
+//      first) so that the lanes of a warp walk lists of nearly equal length,
 //   4. lets every thread walk its vertices' four row ranges as one flat loop,
 //      accumulating s w_i phi_k = s A_x A_y A_z (1, U_x, U_y, U_z, U_x^2/2,
-//      U_y^2/2, U_z^2/2, U_x U_y, U_x U_z, U_y U_z) in registers, with
-//      A_a = 1 - t_a or t_a (corner bit b_a) and U_a = (t_a - b_a) h,
+//      U_y^2/2, U_z^2/2, U_x U_y, U_x U_z, U_y U_z) in registers. With the
+//      local coordinate l of the point and the vertex coordinate v,
+//      d = l - v = t - b exactly (both lie on the FP32 grid of u), so
+//      A = 1 - |d| (= 1 - t or t, exact where t - b is) and U = d h need no
+//      corner bits,
 //   5. stores the sums as the 9^3 tile for one TMA bulk-tensor reduce-add into
 //      the gradient.
 #pragma once
@@ -35,7 +38,7 @@ struct FastLayout {
     static constexpr int NV = K * C;
     static constexpr int BXI = BoxInner<float, NV>::value;
     static constexpr int tile_floats = (kBV * kBV * BXI + 31) / 32 * 32;
-    static constexpr int RS = 4 + (C > 1 ? (C + 3) / 4 * 4 : 0);   // record floats: t (3) and s (C = 1), or t + s block
+    static constexpr int RS = 4 + (C > 1 ? (C + 3) / 4 * 4 : 0);   // record floats: l (3) and s (C = 1), or l + s block
     static constexpr int rec = tile_floats;                          // float offsets
     static constexpr int wtab = rec + kFCap * RS;                    // 64 cell rows x 9 x-positions (row pitch 12)
     static constexpr int cells = wtab + kBrick * kBrick * 12;        // 512 + 1 (+3) counts, then offsets
@@ -102,7 +105,12 @@ brick_bwd_fast_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx
                 for (int ch = 0; ch < C; ++ch) ps[r][ch] = __ldg(dLdf + n * C + ch);
                 const float x[3] = {q.x, q.y, q.z};
                 int c[3];
-                locate<3>(x, res, scale, c, pt[r]);
+                float t[3];
+                locate<3>(x, res, scale, c, t);
+                // local coordinate (c - x0) + t: exact, it is u - x0 on the FP32 grid of u
+                pt[r][0] = (float)(c[0] - x0) + t[0];
+                pt[r][1] = (float)(c[1] - y0) + t[1];
+                pt[r][2] = (float)(c[2] - z0) + t[2];
                 plc[r] = (c[0] - x0) + kBrick * ((c[1] - y0) + kBrick * (c[2] - z0));
                 prk[r] = atomicAdd(cells + plc[r], 1);
             }
@@ -138,10 +146,9 @@ brick_bwd_fast_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx
             unsigned *wr = wtab + 12 * tid;
 #pragma unroll
             for (int vx = 0; vx < kBV; ++vx) {
-                const int lo = o[vx > 0 ? vx - 1 : 0];
-                const int n1 = vx > 0 ? o[vx] - o[vx - 1] : 0;               // cell vx - 1: corner bit b_x = 1
-                const int n0 = vx < kBrick ? o[vx + 1] - o[vx] : 0;          // cell vx: b_x = 0
-                wr[vx] = (unsigned)lo | ((unsigned)n1 << 10) | ((unsigned)n0 << 20);
+                const int lo = o[vx > 0 ? vx - 1 : 0];                      // cells vx - 1 and vx
+                const int hi = o[vx < kBrick ? vx + 1 : kBrick];
+                wr[vx] = (unsigned)lo | ((unsigned)(hi - lo) << 16);
             }
         }
         __syncthreads();
@@ -157,8 +164,7 @@ brick_bwd_fast_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx
             for (int rr = 0; rr < 4; ++rr) {
                 const int cy = vy - (rr & 1), cz = vz - (rr >> 1);
                 if ((unsigned)cy < (unsigned)kBrick && (unsigned)cz < (unsigned)kBrick) {
-                    const unsigned w = wtab[12 * (cy + kBrick * cz) + vx];
-                    load += (int)((w >> 10) & 1023u) + (int)(w >> 20);
+                    load += (int)(wtab[12 * (cy + kBrick * cz) + vx] >> 16);
                 }
             }
             vkey[k] = kMaxLoadBins - 1 - min(load, kMaxLoadBins - 1);          // heaviest first
@@ -193,36 +199,31 @@ brick_bwd_fast_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx
                 dw[rr] = ((unsigned)cy < (unsigned)kBrick && (unsigned)cz < (unsigned)kBrick)
                              ? wtab[12 * (cy + kBrick * cz) + vx] : 0u;
             }
-            int st[4], dd[4], mm[4];
+            int st[4], dd[4];
             int run = 0;
 #pragma unroll
             for (int rr = 0; rr < 4; ++rr) {
-                const int lo = (int)(dw[rr] & 1023u), n1 = (int)((dw[rr] >> 10) & 1023u), n0 = (int)(dw[rr] >> 20);
                 st[rr] = run;
-                dd[rr] = lo - run;                 // slot = j + dd within range rr
-                mm[rr] = run + n1;                 // j < mm: the cell below x (b_x = 1)
-                run += n1 + n0;
+                dd[rr] = (int)(dw[rr] & 0xFFFFu) - run;    // slot = j + dd within range rr
+                run += (int)(dw[rr] >> 16);
             }
             const int e0 = st[1], e1 = st[2], e2 = st[3], total = run;
+            const float fvx = (float)vx, fvy = (float)vy, fvz = (float)vz;
             float acc[NV];
 #pragma unroll
             for (int a = 0; a < NV; ++a) acc[a] = 0.f;
             for (int j = 0; j < total; ++j) {
                 const bool P0 = j >= e0, P1 = j >= e1, P2 = j >= e2;
                 const int d = P2 ? dd[3] : P1 ? dd[2] : P0 ? dd[1] : dd[0];
-                const int m = P2 ? mm[3] : P1 ? mm[2] : P0 ? mm[1] : mm[0];
                 const float *qp = rec + (j + d) * RS;
                 const float4 q = *reinterpret_cast<const float4 *>(qp);
-                const bool cbx = j < m, cbz = P1, cby = P0 ^ P1 ^ P2;
-                const float ax = cbx ? q.x : 1.f - q.x;
-                const float ay = cby ? q.y : 1.f - q.y;
-                const float az = cbz ? q.z : 1.f - q.z;
-                const float w = ax * ay * az;
+                const float dx = q.x - fvx, dy = q.y - fvy, dz = q.z - fvz;      // t - b per axis
+                const float w = (1.f - fabsf(dx)) * (1.f - fabsf(dy)) * (1.f - fabsf(dz));
                 float ux = 0.f, uy = 0.f, uz = 0.f;
                 if constexpr (ORDER >= 1) {
-                    ux = fmaf(q.x, h, cbx ? -h : 0.f);            // (t - b) h
-                    uy = fmaf(q.y, h, cby ? -h : 0.f);
-                    uz = fmaf(q.z, h, cbz ? -h : 0.f);
+                    ux = dx * h;                                    // (t - b) h
+                    uy = dy * h;
+                    uz = dz * h;
                 }
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
