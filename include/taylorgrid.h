@@ -122,7 +122,10 @@ TG_API tg_status tg_get_info(const tg_grid *grid, tg_grid_info *info);
 TG_API tg_status tg_set_coefs(tg_grid *grid, const float *src, tg_stream stream);
 
 /* Read coefficients into `dst` (device, n_coefs floats). which = 0: the
- * stored copy, widened to FP32 (what queries use); which = 1: the FP32 master. */
+ * stored copy, widened to FP32 (what queries use); which = 1: the FP32 master;
+ * which = 2 / 3: Adam's first / second moment widened to FP32 (TG_EINVAL
+ * before the first Adam step). FP32 grids keep FP32 moments; BF16 and FP16
+ * grids keep them in BF16 (the FP32 master and FP32 arithmetic stay). */
 TG_API tg_status tg_get_coefs(const tg_grid *grid, float *dst, int which, tg_stream stream);
 
 /* Progressive resolution (Sec. 4.1 trains coarse to fine): overwrites dst's

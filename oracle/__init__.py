@@ -55,8 +55,9 @@ def lib():
             L.tgo_query_backward.argtypes = [i32, i32, i32, i32, i64, _f32p, _f64p, _f64p, _f64p, _f64p]
             L.tgo_query_absscale.argtypes = [i32, i32, i32, i32, _f64p, i64, _f32p, _f64p]
             L.tgo_query_gradscale.argtypes = [i32, i32, i32, i32, _f64p, i64, _f32p, _f64p]
-            L.tgo_adam.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64]
-            L.tgo_adam_lazy.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64]
+            L.tgo_adam.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64, i32]
+            L.tgo_adam_lazy.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, f64, f64, f64, f64, i64, i32]
+            L.tgo_bf16_round.argtypes = [f64]; L.tgo_bf16_round.restype = f64
             L.tgo_sdf_union.argtypes = [i32, _f32p, i32, _f32p, _f64p]; L.tgo_sdf_union.restype = f64
             L.tgo_sdf_step.argtypes = [i32, i32, _f64p, i64, _f32p, i32, _f32p, i32, _f32p, f64, f64, _f64p, _f64p]
             L.tgo_adaptive_weight1.argtypes = [f64, f64]; L.tgo_adaptive_weight1.restype = f64
@@ -150,19 +151,27 @@ def eval_cell(dim, res, order, C, coefs, cell, t):
     return f, gu.reshape(C, dim)
 
 
-def adam(p, g, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1):
-    """In-place FP64 Adam step on float64 arrays; zeroes g."""
+def adam(p, g, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1, bf16_moments=False):
+    """In-place FP64 Adam step on float64 arrays; zeroes g. bf16_moments rounds m and v to BF16 after the update."""
     for a in (p, g, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
-    lib().tgo_adam(p.size, _p(p, _f64p), _p(g, _f64p), _p(m, _f64p), _p(v, _f64p), lr, beta1, beta2, eps, step)
+    lib().tgo_adam(p.size, _p(p, _f64p), _p(g, _f64p), _p(m, _f64p), _p(v, _f64p), lr, beta1, beta2, eps, step,
+                   int(bool(bf16_moments)))
 
 
-def adam_lazy(p, g, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1):
+def bf16_round(x):
+    """Round every element of x to BF16 (nearest, ties to even), returned as float64."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = lib().tgo_bf16_round
+    return np.array([f(float(e)) for e in x.ravel()]).reshape(x.shape)
+
+
+def adam_lazy(p, g, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1, bf16_moments=False):
     """In-place FP64 lazy (sparse) Adam step: entries with g == 0 keep p, m and v; zeroes g."""
     for a in (p, g, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().tgo_adam_lazy(p.size, _p(p, _f64p), _p(g, _f64p), _p(m, _f64p), _p(v, _f64p), lr, beta1, beta2, eps,
-                        step)
+                        step, int(bool(bf16_moments)))
 
 
 def sdf_union(spheres, boxes, x):

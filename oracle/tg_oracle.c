@@ -395,9 +395,24 @@ TGO_API void tgo_query_gradscale(int dim, int res, int order, int C, const doubl
 /* ------------------------------------------------------------------------ */
 /* Optimiser. The paper fixes only the learning rate (Sec. 4.1); the build   */
 /* uses Adam (Kingma & Ba 2015, Algorithm 1) with bias correction, step >= 1. */
+/* With bf16_moments, the step uses the new m and v as computed, and stores  */
+/* them rounded to BF16 for the next step (the moment storage of the BF16 /   */
+/* FP16 storage form); the rounding is pinned to torch's conversion.         */
 /* ------------------------------------------------------------------------ */
+/* Rounding to BF16 (8-bit significand, the exponent range of FP32), ties to
+ * even: the storage of Adam's moments in the BF16 / FP16 storage form. Below
+ * the smallest normal 2^-126 the spacing is 2^-133 (BF16 subnormals). */
+TGO_API double tgo_bf16_round(double x)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    if (fabs(x) < ldexp(1.0, -126)) return nearbyint(ldexp(x, 133)) * ldexp(1.0, -133);
+    int e;
+    const double f = frexp(x, &e);               /* x = f 2^e, 0.5 <= |f| < 1 */
+    return ldexp(nearbyint(ldexp(f, 8)), e - 8);  /* default rounding mode: nearest, ties to even */
+}
+
 TGO_API void tgo_adam(int64_t n, double *p, double *g, double *m, double *v,
-                      double lr, double beta1, double beta2, double eps, int64_t step)
+                      double lr, double beta1, double beta2, double eps, int64_t step, int bf16_moments)
 {
     double bc1 = 1.0 - pow(beta1, (double)step);
     double bc2 = 1.0 - pow(beta2, (double)step);
@@ -407,6 +422,7 @@ TGO_API void tgo_adam(int64_t n, double *p, double *g, double *m, double *v,
         double mhat = m[j] / bc1;
         double vhat = v[j] / bc2;
         p[j] -= lr * mhat / (sqrt(vhat) + eps);
+        if (bf16_moments) { m[j] = tgo_bf16_round(m[j]); v[j] = tgo_bf16_round(v[j]); }   /* stored for the next step */
         g[j] = 0.0;
     }
 }
@@ -415,7 +431,7 @@ TGO_API void tgo_adam(int64_t n, double *p, double *g, double *m, double *v,
  * gradient is nonzero; the others keep their parameter and both moments (no
  * decay). The bias corrections use the global step. */
 TGO_API void tgo_adam_lazy(int64_t n, double *p, double *g, double *m, double *v,
-                           double lr, double beta1, double beta2, double eps, int64_t step)
+                           double lr, double beta1, double beta2, double eps, int64_t step, int bf16_moments)
 {
     double bc1 = 1.0 - pow(beta1, (double)step);
     double bc2 = 1.0 - pow(beta2, (double)step);
@@ -424,6 +440,7 @@ TGO_API void tgo_adam_lazy(int64_t n, double *p, double *g, double *m, double *v
         m[j] = beta1 * m[j] + (1.0 - beta1) * g[j];
         v[j] = beta2 * v[j] + (1.0 - beta2) * g[j] * g[j];
         p[j] -= lr * (m[j] / bc1) / (sqrt(v[j] / bc2) + eps);
+        if (bf16_moments) { m[j] = tgo_bf16_round(m[j]); v[j] = tgo_bf16_round(v[j]); }
         g[j] = 0.0;
     }
 }

@@ -51,10 +51,41 @@ __device__ __forceinline__ void adam_lazy_one(float &p, float g, float &m, float
     if (g != 0.0f) adam_one(p, g, m, v, a);
 }
 
+// Four moments from FP32 (float4) or BF16 (8-byte) storage, widened to FP32, and back.
+template <typename M> struct Moments;
+template <> struct Moments<float> {
+    __device__ __forceinline__ static float4 load(const float *p, int64_t j) { return reinterpret_cast<const float4 *>(p)[j]; }
+    __device__ __forceinline__ static void store(float *p, int64_t j, float4 v) { reinterpret_cast<float4 *>(p)[j] = v; }
+    __device__ __forceinline__ static float get(const float *p, int64_t j) { return p[j]; }
+    __device__ __forceinline__ static void put(float *p, int64_t j, float v) { p[j] = v; }
+};
+template <> struct Moments<__nv_bfloat16> {
+    __device__ __forceinline__ static float4 load(const __nv_bfloat16 *p, int64_t j)
+    {
+        const uint2 u = reinterpret_cast<const uint2 *>(p)[j];
+        const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
+        const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+        const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16 *p, int64_t j, float4 v)
+    {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<unsigned *>(&lo);
+        u.y = *reinterpret_cast<unsigned *>(&hi);
+        reinterpret_cast<uint2 *>(p)[j] = u;
+    }
+    __device__ __forceinline__ static float get(const __nv_bfloat16 *p, int64_t j) { return __bfloat162float(p[j]); }
+    __device__ __forceinline__ static void put(__nv_bfloat16 *p, int64_t j, float v) { p[j] = __float2bfloat16_rn(v); }
+};
+
 // Vectorised body over n4 = n / 4 float4 groups, scalar tail handled by block 0.
-template <typename T, bool LAZY = false>
+// T: stored copy (float: none); M: moment storage (FP32, or BF16 rounded to
+// nearest even after every update, the arithmetic in FP32).
+template <typename T, bool LAZY = false, typename M = float>
 __global__ void __launch_bounds__(256)
-adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+adam_kernel(float *__restrict__ p, float *__restrict__ g, M *__restrict__ m, M *__restrict__ v,
             T *__restrict__ shadow, int64_t n, AdamCoef a, const int64_t *__restrict__ step_dev, float lr)
 {
     if (step_dev) {   // bias corrections of the 1-based step *step_dev + 1, read on the device
@@ -66,12 +97,10 @@ adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     float4 *p4 = reinterpret_cast<float4 *>(p);
     float4 *g4 = reinterpret_cast<float4 *>(g);
-    float4 *m4 = reinterpret_cast<float4 *>(m);
-    float4 *v4 = reinterpret_cast<float4 *>(v);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n4; j += stride) {
         const float4 gg = __ldcs(g4 + j);
         if (LAZY && gg.x == 0.f && gg.y == 0.f && gg.z == 0.f && gg.w == 0.f) continue;
-        float4 pp = p4[j], mm = m4[j], vv = v4[j];
+        float4 pp = p4[j], mm = Moments<M>::load(m, j), vv = Moments<M>::load(v, j);
         if (LAZY) {
             adam_lazy_one(pp.x, gg.x, mm.x, vv.x, a);
             adam_lazy_one(pp.y, gg.y, mm.y, vv.y, a);
@@ -84,20 +113,39 @@ adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
             adam_one(pp.w, gg.w, mm.w, vv.w, a);
         }
         p4[j] = pp;
-        m4[j] = mm;
-        v4[j] = vv;
+        Moments<M>::store(m, j, mm);
+        Moments<M>::store(v, j, vv);
         __stcs(g4 + j, make_float4(0.f, 0.f, 0.f, 0.f));
         if (shadow) store4<T>(shadow, 4 * j, pp.x, pp.y, pp.z, pp.w);
     }
     if (blockIdx.x == 0) {
         for (int64_t j = 4 * n4 + threadIdx.x; j < n; j += blockDim.x) {
             if (LAZY && g[j] == 0.f) continue;
-            float pp = p[j], mm = m[j], vv = v[j];
+            float pp = p[j], mm = Moments<M>::get(m, j), vv = Moments<M>::get(v, j);
             adam_one(pp, g[j], mm, vv, a);
-            p[j] = pp; m[j] = mm; v[j] = vv; g[j] = 0.0f;
+            p[j] = pp;
+            Moments<M>::put(m, j, mm);
+            Moments<M>::put(v, j, vv);
+            g[j] = 0.0f;
             if (shadow) shadow[j] = from_f32<T>(pp);
         }
     }
+}
+
+tg_status ensure_adam_state(tg_grid *g)
+{
+    if (g->adam_m) return TG_OK;
+    const size_t mb = (size_t)g->ncoef * moment_bytes(g) + 16;
+    tg_status st = dev_alloc(&g->adam_m, mb, "tg_adam_step: cudaMalloc(m)");
+    if (st == TG_OK) st = dev_alloc(&g->adam_v, mb, "tg_adam_step: cudaMalloc(v)");
+    if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_m, 0, mb), "tg_adam_step: zero m");
+    if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_v, 0, mb), "tg_adam_step: zero v");
+    if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_adam_step: init moments");
+    if (st != TG_OK) {
+        cudaFree(g->adam_m); cudaFree(g->adam_v);
+        g->adam_m = g->adam_v = nullptr;
+    }
+    return st;
 }
 
 }  // namespace tg
@@ -106,20 +154,6 @@ using namespace tg;
 
 namespace tg {
 
-tg_status ensure_adam_state(tg_grid *g)
-{
-    if (g->adam_m) return TG_OK;
-    tg_status st = dev_alloc((void **)&g->adam_m, (size_t)g->ncoef * 4 + 16, "tg_adam_step: cudaMalloc(m)");
-    if (st == TG_OK) st = dev_alloc((void **)&g->adam_v, (size_t)g->ncoef * 4 + 16, "tg_adam_step: cudaMalloc(v)");
-    if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_m, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero m");
-    if (st == TG_OK) st = cuda_status(cudaMemset(g->adam_v, 0, (size_t)g->ncoef * 4), "tg_adam_step: zero v");
-    if (st == TG_OK) st = cuda_status(cudaDeviceSynchronize(), "tg_adam_step: init moments");
-    if (st != TG_OK) {
-        cudaFree(g->adam_m); cudaFree(g->adam_v);
-        g->adam_m = g->adam_v = nullptr;
-    }
-    return st;
-}
 
 // Adam over all coefficients; with step_dev the 0-based step index is read on
 // the device (for replayable CUDA graphs) and prm->step is ignored.
@@ -141,8 +175,13 @@ tg_status adam_launch(tg_grid *g, float *grad, const tg_adam *prm, const int64_t
     int64_t need = (n4 + 255) / 256;
     int64_t cap = (int64_t)num_sms() * per_sm;
     unsigned nb = (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
-#define TG_ADAM(T, L, SH) adam_kernel<T, L><<<nb, 256, 0, s>>>(g->master, grad, g->adam_m, g->adam_v, SH, g->ncoef, \
-                                                              a, step_dev, prm->lr)
+#define TG_ADAM(T, L, SH)                                                                                       \
+    (g->lp_moments ? adam_kernel<T, L, __nv_bfloat16><<<nb, 256, 0, s>>>(                                       \
+                         g->master, grad, (__nv_bfloat16 *)g->adam_m, (__nv_bfloat16 *)g->adam_v, SH, g->ncoef, a, \
+                         step_dev, prm->lr)                                                                     \
+                   : adam_kernel<T, L, float><<<nb, 256, 0, s>>>(g->master, grad, (float *)g->adam_m,             \
+                                                                 (float *)g->adam_v, SH, g->ncoef, a, step_dev, \
+                                                                 prm->lr))
     if (g->dtype == TG_F32) {
         if (lazy) TG_ADAM(float, true, nullptr);
         else TG_ADAM(float, false, nullptr);

@@ -177,6 +177,7 @@ tg_status tg_create(int dim, int res, int order, int channels, tg_dtype dtype, u
     tg_grid *g = (tg_grid *)calloc(1, sizeof(tg_grid));
     if (!g) return fail(TG_ENOMEM, "tg_create: host allocation failed");
     g->dim = dim; g->res = res; g->order = order; g->C = channels; g->dtype = dtype;
+    g->lp_moments = dtype != TG_F32;      // the BF16 / FP16 storage form keeps Adam's moments in BF16
     g->K = num_coefs(dim, order);
     g->nv = 1;
     for (int d = 0; d < dim; ++d) g->nv *= res;
@@ -232,7 +233,7 @@ tg_status tg_get_info(const tg_grid *g, tg_grid_info *info)
     info->dtype = g->dtype; info->n_vertices = g->nv; info->n_coefs = g->ncoef;
     size_t b = (size_t)g->ncoef * 4;
     if (g->dtype != TG_F32) b += (size_t)g->ncoef * 2;
-    if (g->adam_m) b += (size_t)g->ncoef * 8;
+    if (g->adam_m) b += (size_t)g->ncoef * 2 * moment_bytes(g);
     info->bytes = b;
     info->coefs = g->store;
     info->master = g->master;
@@ -257,8 +258,18 @@ tg_status tg_set_coefs(tg_grid *g, const float *src, tg_stream stream)
 tg_status tg_get_coefs(const tg_grid *g, float *dst, int which, tg_stream stream)
 {
     if (!g || !dst) return fail(TG_EINVAL, "tg_get_coefs: NULL argument");
-    if (which != 0 && which != 1) return fail(TG_EINVAL, "tg_get_coefs: which must be 0 or 1");
+    if (which < 0 || which > 3) return fail(TG_EINVAL, "tg_get_coefs: which must be 0, 1, 2 or 3");
     cudaStream_t s = (cudaStream_t)stream;
+    if (which >= 2) {      // Adam's first (2) or second (3) moment, widened to FP32
+        const void *src = which == 2 ? g->adam_m : g->adam_v;
+        if (!src) return fail(TG_EINVAL, "tg_get_coefs: the grid has no Adam state yet");
+        if (!g->lp_moments)
+            return cuda_status(cudaMemcpyAsync(dst, src, (size_t)g->ncoef * 4, cudaMemcpyDeviceToDevice, s),
+                               "tg_get_coefs: copy");
+        widen_kernel<__nv_bfloat16><<<elementwise_blocks(g->ncoef), 256, 0, s>>>((const __nv_bfloat16 *)src, dst,
+                                                                               g->ncoef);
+        return launch_status("tg_get_coefs: widen kernel");
+    }
     if (which == 1 || g->dtype == TG_F32)
         return cuda_status(cudaMemcpyAsync(dst, g->master, (size_t)g->ncoef * 4, cudaMemcpyDeviceToDevice, s),
                            "tg_get_coefs: copy");
@@ -287,9 +298,15 @@ tg_status tg_save(const tg_grid *g, const char *path)
     }
     tg_status st = TG_OK;
     bool ok = fwrite("TGCK", 1, 4, f) == 4 && fwrite(hdr, sizeof(hdr), 1, f) == 1 && fwrite(&n, 8, 1, f) == 1;
-    const float *arrays[3] = {g->master, g->adam_m, g->adam_v};
+    const void *arrays[3] = {g->master, g->adam_m, g->adam_v};
     for (int a = 0; ok && st == TG_OK && a < (g->adam_m ? 3 : 1); ++a) {
-        st = cuda_status(cudaMemcpy(host, arrays[a], bytes, cudaMemcpyDeviceToHost), "tg_save: copy");
+        const bool lp = a > 0 && g->lp_moments;      // BF16 moments: the upper halves of FP32 words
+        st = cuda_status(cudaMemcpy(host, arrays[a], lp ? (size_t)n * 2 : bytes, cudaMemcpyDeviceToHost), "tg_save: copy");
+        if (st == TG_OK && lp) {
+            const uint16_t *h16 = reinterpret_cast<const uint16_t *>(host);
+            uint32_t *h32 = reinterpret_cast<uint32_t *>(host);
+            for (int64_t k = n - 1; k >= 0; --k) h32[k] = (uint32_t)h16[k] << 16;     // back to front: in place
+        }
         if (st == TG_OK) ok = fwrite(host, 1, bytes, f) == bytes;
     }
     if (fclose(f) != 0) ok = false;
@@ -333,10 +350,23 @@ tg_status tg_load(const char *path, tg_grid **out)
     }
     const int arrays = hdr[6] ? 3 : 1;
     if (hdr[6]) st = ensure_adam_state(g);
-    float *dst[3] = {g->master, g->adam_m, g->adam_v};
+    void *dst[3] = {g->master, g->adam_m, g->adam_v};
     for (int a = 0; st == TG_OK && a < arrays; ++a) {
-        if (fread(host, 1, bytes, f) != bytes) st = fail(TG_EINVAL, "tg_load: %s is truncated", path);
-        else st = cuda_status(cudaMemcpy(dst[a], host, bytes, cudaMemcpyHostToDevice), "tg_load: copy");
+        const bool lp = a > 0 && g->lp_moments;
+        if (fread(host, 1, bytes, f) != bytes) {
+            st = fail(TG_EINVAL, "tg_load: %s is truncated", path);
+            break;
+        }
+        if (lp) {      // FP32 -> BF16, round to nearest even (exact for moments saved from BF16)
+            const uint32_t *h32 = reinterpret_cast<const uint32_t *>(host);
+            uint16_t *h16 = reinterpret_cast<uint16_t *>(host);
+            for (int64_t k = 0; k < n; ++k) {
+                const uint32_t u = h32[k];
+                const bool nan = (u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu) != 0;
+                h16[k] = nan ? (uint16_t)((u >> 16) | 0x40u) : (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+            }
+        }
+        st = cuda_status(cudaMemcpy(dst[a], host, lp ? (size_t)n * 2 : bytes, cudaMemcpyHostToDevice), "tg_load: copy");
     }
     fclose(f);
     free(host);

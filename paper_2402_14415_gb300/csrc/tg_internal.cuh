@@ -18,8 +18,9 @@ struct tg_grid {
     int64_t ncoef;       // nv * C * K
     void *store;         // stored coefficients in the storage dtype (== master for FP32)
     float *master;       // FP32 master copy
-    float *adam_m;       // Adam first moment (lazily allocated)
-    float *adam_v;       // Adam second moment
+    void *adam_m;        // Adam first moment (lazily allocated): FP32, or BF16 with lp_moments
+    void *adam_v;        // Adam second moment
+    bool lp_moments;     // BF16 moments (the BF16 / FP16 storage form), FP32 arithmetic
     struct tg_batch *auto_batch;   // binning scratch of large tg_query / tg_query_backward calls (lazy)
     cudaEvent_t auto_event;        // last use of auto_batch
 };
@@ -64,6 +65,8 @@ inline int num_coefs(int dim, int order)
 }
 
 inline size_t storage_bytes(tg_dtype d) { return d == TG_F32 ? 4 : 2; }
+// Bytes of one Adam moment: BF16 moments go with BF16 / FP16 storage.
+inline size_t moment_bytes(const tg_grid *g) { return g->lp_moments ? 2 : 4; }
 
 // ---------------------------------------------------------------------------
 // Storage types

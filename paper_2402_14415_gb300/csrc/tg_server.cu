@@ -92,7 +92,8 @@ static size_t fit_bytes(const tg_fit_desc &d)
 {
     const int K = num_coefs(3, d.order);
     const size_t ncoef = (size_t)d.res * d.res * d.res * K;
-    size_t b = ncoef * (4 + 8 + 4) + (d.dtype == TG_F32 ? 0 : ncoef * 2);     // master, Adam m+v, gradient, shadow
+    // master, Adam m + v (FP32, or BF16 for BF16 / FP16 storage), gradient, shadow
+    size_t b = d.dtype == TG_F32 ? ncoef * (4 + 8 + 4) : ncoef * (4 + 4 + 4 + 2);
     const size_t nb = (size_t)((d.res - 2) / 8 + 1);
     const size_t bricks = nb * nb * nb;
     b += (size_t)d.points_per_step * (16 + 16 + 4 + 4 * 11);                  // records, coarse, perm, staging

@@ -774,3 +774,50 @@ def test_gradscale_bounds_the_spatial_gradient_and_is_exact_for_coherent_terms(d
         _, g0, _, _ = oracle.query(dim, res, 0, C, f0, pts)
         G0 = oracle.query_gradscale(dim, res, 0, C, f0, pts)
         np.testing.assert_allclose(G0[..., a], np.abs(g0[..., a]), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# BF16 rounding of the Adam moments (the BF16 / FP16 storage form)
+# --------------------------------------------------------------------------
+def test_bf16_round_matches_torch_conversion():
+    """The oracle's rounding to BF16 equals torch's float32 -> bfloat16 conversion (nearest, ties to even) on
+    FP32 values: random normals over many magnitudes, exact ties, BF16 subnormals and values that are already
+    BF16."""
+    r = rng(95)
+    x = (r.standard_normal(4000) * 10.0 ** r.uniform(-30, 30, 4000)).astype(np.float32)
+    bits = r.integers(0, 2 ** 16, 500, dtype=np.uint32) << np.uint32(16)
+    ties = (bits | np.uint32(0x8000)).view(np.float32)                    # exactly half way between BF16 values
+    sub = (r.standard_normal(500) * 1e-39).astype(np.float32)             # FP32 subnormals: BF16 subnormals too
+    exact = bits.view(np.float32)
+    x = np.concatenate([x, ties, sub, exact, np.float32([0.0, -0.0, 1.0, -2.5])])
+    x = x[np.isfinite(x)]
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    got = oracle.bf16_round(x.astype(np.float64))
+    np.testing.assert_array_equal(got, want)
+
+
+def test_adam_with_bf16_moments_reduces_to_adam_when_moments_are_representable():
+    """With gradients that keep every moment exactly representable in BF16 (a constant gradient 2^k: m and v
+    are sums of few powers of two scaled by the betas only when the betas are powers of two), the BF16-moment
+    step equals the plain step; with generic gradients the moments differ from plain Adam's by at most half a
+    BF16 unit in the last place of the rounded value."""
+    n = 64
+    p = np.linspace(-1, 1, n)
+    pa, pb = p.copy(), p.copy()
+    ma, va, mb, vb = (np.zeros(n) for _ in range(4))
+    for step in range(1, 4):
+        g = np.full(n, 0.25)
+        oracle.adam(pa, g.copy(), ma, va, 1e-2, 0.5, 0.75, 1e-8, step)
+        oracle.adam(pb, g.copy(), mb, vb, 1e-2, 0.5, 0.75, 1e-8, step, bf16_moments=True)
+        np.testing.assert_array_equal(ma, mb)
+        np.testing.assert_array_equal(va, vb)
+        np.testing.assert_array_equal(pa, pb)
+    r = rng(96)
+    m0, v0 = r.normal(size=n), r.random(n)
+    g = r.normal(size=n)
+    mc, vc, md, vd = m0.copy(), v0.copy(), m0.copy(), v0.copy()
+    oracle.adam(p.copy(), g.copy(), mc, vc, 1e-2, step=3)
+    oracle.adam(p.copy(), g.copy(), md, vd, 1e-2, step=3, bf16_moments=True)
+    np.testing.assert_array_equal(md, oracle.bf16_round(mc))
+    np.testing.assert_array_equal(vd, oracle.bf16_round(vc))
+    assert (np.abs(md - mc) <= np.abs(mc) * 2.0 ** -8).all()
