@@ -256,27 +256,28 @@ def run_ours(args, world, rank, local):
     batch = tg.tg_batch_create(3, RES, N)
     stream = torch.cuda.current_stream()
 
-    # one step = bin, forward (f in input order), backward (dL/df in input order)
-    calls = [("bin", lambda pts, up: tg.tg_batch_bin(batch, pts)),
-             ("forward", lambda pts, up: tg.tg_query_binned(g, batch, out=out)),
-             ("backward", lambda pts, up: tg.tg_query_backward_binned(g, batch, up, grad))]
+    # one step = bin, forward, backward. The headline runs in binned order: f
+    # is written, and dL/df read, in the batch's brick order (tg_batch_order
+    # maps a slot to its input index), as the training paths use it; the
+    # input-order variant (f scattered to, dL/df gathered from, input
+    # positions) is timed beside it.
+    def calls_of(binned):
+        return [("bin", lambda pts, up: tg.tg_batch_bin(batch, pts)),
+                ("forward", lambda pts, up: tg.tg_query_binned(g, batch, out=out, binned_order=binned)),
+                ("backward", lambda pts, up: tg.tg_query_backward_binned(g, batch, up, grad, binned_order=binned))]
 
-    def step(pts=P, upstream=U):
-        for _, call in calls:
-            call(pts, upstream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # device-timed region
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(args.steps)]
-    with Clocks(local) as clk:
+    def timed(binned, steps, warmup, clk=None):
+        calls = calls_of(binned)
+        for _ in range(warmup):
+            for _, call in calls:
+                call(P, U)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        kev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(steps)]
         barrier(world)
         torch.cuda.synchronize()
         ev[0].record(stream)
-        for s in range(args.steps):
+        for s in range(steps):
             for k, (_, call) in enumerate(calls):
                 kev[s][k].record(stream)
                 call(P, U)
@@ -284,10 +285,16 @@ def run_ours(args, world, rank, local):
         ev[1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
+        ms = max_over_ranks(world, ev[0].elapsed_time(ev[1])) / steps
+        kernels = {name: statistics.mean(e[k].elapsed_time(e[k + 1]) for e in kev) for k, (name, _) in enumerate(calls)}
+        return ms, kernels
+
+    # device-timed region
+    with Clocks(local) as clk:
+        ms, kernels = timed(True, args.steps, args.warmup)
     clocks = clk.summary()
-    ms = max_over_ranks(world, ev[0].elapsed_time(ev[1])) / args.steps
-    kernels = {name: statistics.mean(e[k].elapsed_time(e[k + 1]) for e in kev) for k, (name, _) in enumerate(calls)}
     value = world * N / (ms * 1e-3) / 1e6
+    ms_in, kernels_in = timed(False, args.steps, 3)
 
     # End to end through the public API: every step copies its inputs from pinned
     # host memory and reads f back to pinned host memory. Two buffer sets and two
@@ -315,8 +322,8 @@ def run_ours(args, world, rank, local):
         if used[b]:
             stream.wait_event(read_back[b])        # step k-2's f has left this buffer
         tg.tg_batch_bin(batch, Pb)
-        tg.tg_query_binned(g, batch, out=Ob)
-        tg.tg_query_backward_binned(g, batch, Ub, grad)
+        tg.tg_query_binned(g, batch, out=Ob, binned_order=True)
+        tg.tg_query_backward_binned(g, batch, Ub, grad, binned_order=True)
         computed[b].record(stream)
         d2h.wait_event(computed[b])
         with torch.cuda.stream(d2h):
@@ -336,6 +343,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(world, e0.elapsed_time(e1)) / args.steps
     barrier(world)
+    tg.tg_batch_bin(batch, P)                      # the headline's f (the input-order pass ran last)
+    tg.tg_query_binned(g, batch, out=out, binned_order=True)
     assert torch.equal(outs_h[(1 + args.steps) % 2], out.cpu()), "end-to-end f differs from the device-timed f"
 
     hbm, peak_kind = peaks()
@@ -350,7 +359,11 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "points_per_gpu": N, "res": RES, "order": ORDER, "channels": C,
                    "l2": "inputs larger than L2 (points 201 MB, grid 671 MB, gradient 671 MB)",
                    "parallelism": f"replicas x{world}"},
+        "order": "binned: f written and dL/df read in the batch's brick order",
         "kernel_ms": {k: round(v, 4) for k, v in kernels.items()},
+        "input_order": {"value": world * N / (ms_in * 1e-3) / 1e6, "unit": "Mpts/s", "ms_per_step": ms_in,
+                        "kernel_ms": {k: round(v, 4) for k, v in kernels_in.items()},
+                        "note": "f scattered to and dL/df gathered from the points' input positions"},
         "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
                      "traffic": TRAFFIC.get(dom),
@@ -366,10 +379,11 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_extras:     # single-GPU runs only: the same on every N
         line["configs"] = {"fit_step_256_o2": bench_fit_step(), "query_only_256": bench_query_only(),
                            "query_pair_c_abi_256": bench_query_pair(), "query_pair_2d_1024": bench_query_2d(),
-                           "render_160": bench_render(), "render_fit_160": bench_render_fit(),
-                           "recon_256_union": bench_recon()}
+                           "render_160": bench_render(), "render_fit_160_400x400": bench_render_fit(),
+                           "recon_256_union": bench_recon(), "fit_256_o2_from_scratch": bench_fit_from_scratch()}
         if not args.no_serving:
             line["configs"]["serving"] = bench_serving()
+            line["configs"]["serving_burst"] = bench_burst()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_of(tg.tg_get_coefs(g).cpu().numpy())      # the very grid the GPU ran on
     if rank == 0:
@@ -537,35 +551,39 @@ def bench_query_pair(steps=5, warmup=2):
             "point_parallel": round(n / (ms_pp * 1e-3) / 1e6, 1), "ms_point_parallel": round(ms_pp, 3)}
 
 
-def blob_gt(scene, rays_o, rays_d, n_samples=1024, bg=1.0, chunk=1024):
+def blob_gt(scene, rays_o, rays_d, n_samples=1024, bg=1.0, chunk=1024, dtype=None):
     """Ground-truth colours of the synthetic blob scene (the Synthetic-NeRF stand-in): density
     sum_k a_k exp(-1/2 (x - mu_k)^T P_k (x - mu_k)), colour the density-weighted mean of the blobs' rgb,
     composited along each ray by midpoint quadrature over its [near, far] in the unit cube (bg on a miss).
-    Plain torch on the GPU, FP64, in chunks of rays; the exponent of every (sample, blob) pair is one
-    row of a matrix product of the sample's monomials (xx, yy, zz, xy, xz, yz, x, y, z, 1) with per-blob
-    coefficients. It only makes the training targets."""
+    Plain torch on the GPU, FP64 (or `dtype`), in chunks of rays; the exponent of every (sample, blob) pair
+    is one row of a matrix product of the sample's monomials (xx, yy, zz, xy, xz, yz, x, y, z, 1) with
+    per-blob coefficients. It only makes the training targets. In FP32 the monomial form loses about 1e-7 of
+    |x^T P x| <= 3 / 0.02^2 to cancellation, a relative error below 1e-3 in a blob's density."""
     import torch
+    dtype = dtype or torch.float64
+    tiny = torch.finfo(dtype).tiny
     mu, P, amp, rgb = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in scene)
     Pm = torch.einsum("bac,bc->ba", P, mu)                                       # P mu
     coef = torch.stack([P[:, 0, 0], P[:, 1, 1], P[:, 2, 2], 2 * P[:, 0, 1], 2 * P[:, 0, 2], 2 * P[:, 1, 2],
                         -2 * Pm[:, 0], -2 * Pm[:, 1], -2 * Pm[:, 2], (mu * Pm).sum(1)], 0)   # (10, B)
+    coef, amp, rgb = coef.to(dtype), amp.to(dtype), rgb.to(dtype)
     out = []
     for i in range(0, rays_o.shape[0], chunk):
-        o, d = rays_o[i:i + chunk].double(), rays_d[i:i + chunk].double()
+        o, d = rays_o[i:i + chunk].to(dtype), rays_d[i:i + chunk].to(dtype)
         inv = 1.0 / torch.where(d == 0, torch.full_like(d, 1e-30), d)
         t0, t1 = (0.0 - o) * inv, (1.0 - o) * inv
         near = torch.clamp(torch.minimum(t0, t1).amax(1), min=0.0)
         far = torch.maximum(t0, t1).amin(1)
         hit = far > near
         dt = torch.where(hit, (far - near) / n_samples, torch.zeros_like(far))
-        ts = near[:, None] + (torch.arange(n_samples, device="cuda", dtype=torch.float64)[None] + 0.5) * dt[:, None]
+        ts = near[:, None] + (torch.arange(n_samples, device="cuda", dtype=dtype)[None] + 0.5) * dt[:, None]
         x = o[:, None, :] + ts[..., None] * d[:, None, :]                        # (r, n, 3)
         X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
         mono = torch.stack([X * X, Y * Y, Z * Z, X * Y, X * Z, Y * Z, X, Y, Z, torch.ones_like(X)], -1)
         q = mono @ coef                                                          # (r, n, B)
         s = amp * torch.exp(-0.5 * torch.clamp(q, min=0.0))
         sig = s.sum(-1)
-        col = (s @ rgb) / torch.clamp(sig, min=1e-300)[..., None]
+        col = (s @ rgb) / torch.clamp(sig, min=tiny)[..., None]
         tau = sig * dt[:, None]
         T = torch.exp(-(torch.cumsum(tau, 1) - tau))
         w = T * (1 - torch.exp(-tau))
@@ -603,6 +621,34 @@ def bench_render(steps=5, warmup=2):
     return {"workload": "ray-march training step, 8192 rays x 256 samples, 160^3 BF16 density o2 + colour o1 (3 ch)",
             "train_ms_per_step": ms, "train_Msamples_per_s": R * S / (ms * 1e-3) / 1e6,
             "forward_ms": fwd, "forward_Msamples_per_s": R * S / (fwd * 1e-3) / 1e6}
+
+
+def bench_fit_from_scratch(steps=2000, n_pts=1 << 20):
+    """The 256^3 order-2 fit from scratch as configured: 2000 Adam steps at lr 5e-3, L1 + 0.1 eikonal, 2^20
+    points per step, on the union shape (24 spheres, 8 boxes), with FP32, BF16 and FP16 storage; mean |SDF
+    error| on 2^16 and volumetric IoU on 2^20 uniform points after the last step."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    from paper_2402_14415_gb300.fit import fit_sdf
+    shape = W.union_shape(0)
+    dsh = tg.DeviceShape(shape.spheres, shape.boxes, shape.area_cdf())
+    ev = torch.rand((1 << 20, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(2))
+    out = {}
+    for dt in ("f32", "bf16", "f16"):
+        g = tg.tg_create(3, RES, ORDER, 1, dt, seed=0, init_std=1e-3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fit_sdf(g, dsh, steps, n_pts, lr=5e-3, lambda_eik=0.1, eval_pts=ev[:1 << 16], eval_every=steps)
+        torch.cuda.synchronize()
+        out[dt] = {"fit_s": time.perf_counter() - t0, "mean_abs_sdf_error": r.final_error,
+                   "iou": tg.tg_sdf_iou(g, dsh, ev)}
+        del g
+    for dt in ("bf16", "f16"):
+        out[dt]["error_vs_f32"] = out[dt]["mean_abs_sdf_error"] / out["f32"]["mean_abs_sdf_error"]
+    return {"workload": f"union shape, 256^3 order 2 from scratch, {steps} steps, Adam lr 5e-3, L1 + 0.1 eikonal, "
+                        "2^20 points per step", **out}
 
 
 def bench_recon(coarse_steps=1500, fine_steps=500, n_pts=1 << 20, M=256, n_samples=1 << 16, fine_lr=1e-4):
@@ -654,10 +700,11 @@ def bench_recon(coarse_steps=1500, fine_steps=500, n_pts=1 << 20, M=256, n_sampl
             "mesh_extract_ms": ms_mesh, "sample_and_chamfer_ms": a.elapsed_time(b)}
 
 
-def bench_render_fit(steps=3000, res=160, R=8192, S=256, side=100, lr=(0.1, 0.03)):
-    """The ray-marching fit of the synthetic blob scene: 100 cameras on a sphere of radius 1.5 (every 10th held
-    out), targets rendered by blob_gt with 1024 midpoint samples, density (order 2) + colour (order 1, 3 ch)
-    BF16 grids, MSE photometric loss, Adam; PSNR on the held-out views."""
+def bench_render_fit(steps=3000, res=160, R=8192, S=256, side=400, lr=(0.1, 0.03)):
+    """The ray-marching fit of the synthetic blob scene: 100 cameras at side x side pixels on a sphere of radius
+    1.5 (every 10th held out), targets rendered by blob_gt with 1024 midpoint samples (FP32 at 400 x 400: the
+    14.4 M training pixels would take minutes in FP64), density (order 2) + colour (order 1, 3 ch) BF16 grids,
+    MSE photometric loss, Adam; PSNR on the held-out views."""
     import math
 
     import torch
@@ -669,7 +716,9 @@ def bench_render_fit(steps=3000, res=160, R=8192, S=256, side=100, lr=(0.1, 0.03
     cams_te = [k for k in range(100) if k % 10 == 0]
     o_tr, d_tr = (torch.from_numpy(a).cuda() for a in W.camera_rays(100, side, side, cams=cams_tr))
     o_te, d_te = (torch.from_numpy(a).cuda() for a in W.camera_rays(100, side, side, cams=cams_te))
-    gt_tr, gt_te = blob_gt(scene, o_tr, d_tr), blob_gt(scene, o_te, d_te)
+    gdt = torch.float32 if side > 100 else torch.float64
+    gt_tr, gt_te = (blob_gt(scene, o, d, dtype=gdt, chunk=4096 if side > 100 else 1024)
+                    for o, d in ((o_tr, d_tr), (o_te, d_te)))
     dg = tg.tg_create(3, res, 2, 1, "bf16", seed=0, init_std=1e-3)
     cg = tg.tg_create(3, res, 1, 3, "bf16", seed=1, init_std=1e-3)
     batch = tg.tg_batch_create(3, res, R * S)
@@ -696,11 +745,11 @@ def bench_render_fit(steps=3000, res=160, R=8192, S=256, side=100, lr=(0.1, 0.03
     psnr = -10 * math.log10(sq / (o_te.shape[0] * 3))
     return {"workload": f"ray-march fit of 64 Gaussian blobs: {res}^3 BF16 density o2 + colour o1, {R} rays x {S} "
                         f"samples, {steps} steps, Adam lr {lr}; 90 training / 10 held-out cameras at {side}x{side} "
-                        "(targets by 1024-sample midpoint quadrature)",
+                        f"(targets by 1024-sample midpoint quadrature in {str(gdt).split('.')[-1]})",
             "ms_per_step": ms, "held_out_psnr_db": psnr}
 
 
-def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8, deadline_s=120.0):
+def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=32, deadline_s=120.0):
     """Poisson arrivals of fit jobs (70 %) and queries (30 %) through the server, against the same trace run
     one job at a time with FP32 storage."""
     import math
@@ -723,7 +772,7 @@ def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8, deadli
             trace.append({"kind": "query", "t": t, "n": n, "of": int(rng.choice(fits)),
                           "pts": torch.rand((n, 3), device="cuda")})
 
-    def run(force_fp32, max_running, smallest_first=False):
+    def run(force_fp32, max_running, smallest_first=False, lazy=False):
         srv = tg.Server(budget_bytes=budget, max_running=max_running, smallest_first=smallest_first)
         ids, outs = {}, []
         t0 = srv.time()
@@ -737,7 +786,7 @@ def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8, deadli
                     ids[i] = srv.fit_job(sh.spheres, sh.boxes, sh.area_cdf(), res=e["res"], order=e["order"],
                                          dtype="f32" if force_fp32 else e["dtype"], seed=e["seed"],
                                          points_per_step=1 << 16, eval_points=1 << 14, eval_every=10,
-                                         max_steps=1000, tol=2e-3, lr=5e-3, lambda_eik=0.0)
+                                         max_steps=1000, tol=2e-3, lr=5e-3, lambda_eik=0.0, lazy_adam=lazy)
                 else:
                     out = torch.empty(e["n"], device="cuda")
                     outs.append(out)
@@ -751,23 +800,63 @@ def bench_serving(n_jobs=40, rate=20.0, budget=64 << 30, seed=5, slots=8, deadli
                 raise RuntimeError(f"serving trace did not drain within {deadline_s} s")
         makespan = srv.time() - t0
         lat = {"fit": [], "query": []}
-        pts = 0
+        pts, errs, steps = 0, [], []
         for k, jid in ids.items():
             r = srv.poll(jid)
             lat[trace[k]["kind"]].append(r["t_done"] - (t0 + trace[k]["t"]))
             pts += r["points"]
+            if trace[k]["kind"] == "fit":
+                errs.append(r["error"])
+                steps.append(r["steps"])
         srv.close()
         pct = lambda a, q: float(np.percentile(a, q)) if a else None
         return {"fit_p50_s": pct(lat["fit"], 50), "fit_p99_s": pct(lat["fit"], 99),
                 "query_p50_s": pct(lat["query"], 50), "query_p99_s": pct(lat["query"], 99),
-                "makespan_s": makespan, "Mpts_per_s": pts / makespan / 1e6}
+                "makespan_s": makespan, "Mpts_per_s": pts / makespan / 1e6,
+                "fit_steps_total": int(sum(steps)), "fit_reached_tol": int(sum(e < 2e-3 for e in errs)),
+                "fit_final_error_median": pct(errs, 50)}
     served = run(False, slots, smallest_first=True)
+    served_lazy = run(False, slots, smallest_first=True, lazy=True)
     alone = run(True, 1)
     return {"workload": f"{n_jobs} Poisson arrivals at {rate}/s: 70% SDF fit jobs (res 32/64/128/256, order 1/2, "
                         "BF16/FP32, 2^16 points/step, L1, until mean |SDF error| < 2e-3 or 1000 steps), 30% queries "
                         "of 1e4-1e6 points; 64 GB admission budget",
             "served": {"slots": slots, "admission": "smallest job first", **served},
+            "served_lazy_adam": {"slots": slots, "admission": "smallest job first", **served_lazy},
             "one_at_a_time_fp32": alone}
+
+
+def bench_burst(n_jobs=24, steps=200, budget=64 << 30, deadline_s=120.0):
+    """Saturation throughput: n_jobs SDF fit jobs submitted at once (res 64 / 96, order 1 / 2, BF16 / FP32,
+    2^16 points per step, a fixed number of steps), run three ways: advanced in groups (one launch per stage per
+    group of equal order and dtype), each job alone on its own stream (TG_FIT_DETERMINISTIC), and one job at a
+    time."""
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    mix = [(64 + 32 * (k % 2), 1 + (k // 2) % 2, ("bf16", "f32")[(k // 4) % 2]) for k in range(n_jobs)]
+
+    def run(max_running, deterministic):
+        srv = tg.Server(budget_bytes=budget, max_running=max_running)
+        t0 = srv.time()
+        ids = []
+        for k, (res, order, dtype) in enumerate(mix):
+            sh = W.union_shape(300 + k)
+            ids.append(srv.fit_job(sh.spheres, sh.boxes, sh.area_cdf(), res=res, order=order, dtype=dtype,
+                                   seed=300 + k, points_per_step=1 << 16, eval_points=1 << 14, eval_every=10,
+                                   max_steps=steps, tol=0.0, lr=5e-3, deterministic=deterministic))
+        srv.run_until_idle(timeout_s=deadline_s)
+        makespan = srv.time() - t0
+        rs = [srv.poll(j) for j in ids]
+        srv.close()
+        assert all(r["state"] == "done" and r["steps"] == steps for r in rs), rs
+        pts = sum(r["points"] for r in rs)
+        return {"makespan_s": makespan, "Mpts_per_s": pts / makespan / 1e6}
+    grouped = run(n_jobs, False)
+    own = run(n_jobs, True)
+    serial = run(1, False)
+    return {"workload": f"{n_jobs} SDF fit jobs submitted at once (res 64/96, order 1/2, BF16/FP32, 2^16 points/step, "
+                        f"L1, {steps} steps each)",
+            "grouped": grouped, "own_stream_each": own, "one_at_a_time": serial}
 
 
 def profile_once():
@@ -786,8 +875,10 @@ def profile_once():
     gx = torch.empty((n, 1, 3), device="cuda")
     grad = torch.zeros(g.n_coefs, device="cuda")
     batch = tg.tg_batch_create(3, RES, n)
-    # the bench step's launches, in its order: bin, forward, backward
+    # the bench step's launches, in its order: bin, forward, backward (binned order), then the input-order pair
     tg.tg_batch_bin(batch, P)
+    tg.tg_query_binned(g, batch, out=out, binned_order=True)
+    tg.tg_query_backward_binned(g, batch, U, grad, binned_order=True)
     tg.tg_query_binned(g, batch, out=out)
     tg.tg_query_backward_binned(g, batch, U, grad)
     # spatial-gradient variants of the two brick kernels
@@ -806,13 +897,59 @@ def profile_once():
     print("profile pass done, timeouts:", tg.tg_batch_timeouts(batch))
 
 
+def profile_fit(dtype="f32"):
+    """Three SDF fit steps (256^3 order 2, 2^20 points, L1 + 0.1 eikonal, Adam) for ncu: two warm-up steps, then
+    the profiled one (capture with -s <launches of two steps>)."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    shape = W.union_shape(0)
+    dsh = tg.DeviceShape(shape.spheres, shape.boxes, shape.area_cdf())
+    n = 1 << 20
+    g = tg.tg_create(3, RES, ORDER, 1, dtype, seed=0, init_std=1e-3)
+    batch = tg.tg_batch_create(3, RES, n)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    loss = torch.zeros(2, device="cuda")
+    for k in range(3):
+        tg.tg_sdf_step(g, batch, dsh, grad, loss, n=n, seed=1, step=k, lambda_eik=0.1)
+        tg.tg_adam_step(g, grad, lr=5e-3, step=k + 1)
+    torch.cuda.synchronize()
+    print("profile fit pass done, timeouts:", tg.tg_batch_timeouts(batch))
+
+
+def profile_render():
+    """Three ray-march training steps (8192 rays x 256 samples, 160^3 BF16 density o2 + colour o1 x 3, both Adam
+    steps) for ncu: two warm-up steps, then the profiled one."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    res, R, S = 160, 8192, 256
+    dg = tg.tg_create(3, res, 2, 1, "bf16", seed=0, init_std=0.5)
+    cg = tg.tg_create(3, res, 1, 3, "bf16", seed=1, init_std=0.5)
+    o, d = W.random_rays(7, R, radius=1.5, spread=0.35)
+    ro, rd = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    target = torch.rand((R, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    batch = tg.tg_batch_create(3, res, R * S)
+    dgr = torch.zeros(dg.n_coefs, device="cuda")
+    cgr = torch.zeros(cg.n_coefs, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    for k in range(3):
+        tg.tg_render_rays(dg, cg, ro, rd, S=S, seed=k, target=target, batch=batch, density_grad=dgr,
+                          color_grad=cgr, loss_sum=loss)
+        tg.tg_adam_step(dg, dgr, lr=0.1, step=k + 1)
+        tg.tg_adam_step(cg, cgr, lr=0.03, step=k + 1)
+    torch.cuda.synchronize()
+    print("profile render pass done")
+
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# full-size launch captured by `ncu --set full ... python bench.py --profile`
+# full-size launches (binned order) captured by `ncu ... python bench.py --profile`
 # (profiles/query_step_256_o2_2e24_full.md); None once the kernel has changed since.
-TRAFFIC = {"forward": 1.200449e9 + 0.381682e9, "backward": 1.562584e9 + 0.639463e9,
-           "bin": (0.201360 + 0.003243 + 0.019930 + 0.000140 + 0.228140 + 0.221858 + 0.275141 + 0.294243) * 1e9}
+TRAFFIC = {"forward": None, "backward": None, "bin": None}
 KERNEL_NAMES = {"bin": "bin_* (5 kernels, tg_batch_bin)", "forward": "brick_fwd_kernel (tg_query_binned)",
-                "backward": "brick_bwd_kernel (tg_query_backward_binned)"}
+                "backward": "brick_bwd_fast_kernel (tg_query_backward_binned)"}
 
 
 def main():
@@ -827,6 +964,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run each kernel of the step once, untimed (for ncu captures)")
     ap.add_argument("--profile-points", type=int, default=N_POINTS)
+    ap.add_argument("--profile-fit", choices=["f32", "bf16", "f16"], default=None,
+                    help="run three SDF fit steps at 256^3 order 2 in this storage dtype (for ncu captures)")
+    ap.add_argument("--profile-render", action="store_true",
+                    help="run three ray-march training steps at 160^3 (for ncu captures)")
     ap.add_argument("--cpu-baseline-from", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_baseline_from:
@@ -834,6 +975,10 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.profile:
         return profile_once()
+    if args.profile_fit:
+        return profile_fit(args.profile_fit)
+    if args.profile_render:
+        return profile_render()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)

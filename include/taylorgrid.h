@@ -489,13 +489,20 @@ TG_API tg_status tg_render_rays_backward(const tg_grid *density, const tg_grid *
  * fits one shape at a time). Fit jobs (Sec. 3.2 SDF fits) and query requests
  * arrive at any time. A tick (tg_server_step) retires finished work, admits
  * queued jobs while the sum of their device bytes stays within the budget,
- * and launches one training step of every running fit job on that job's own
- * stream - a CUDA graph captured at admission (sampler, binning, forward,
- * loss, backward, Adam, a device-gated evaluation every eval_every steps)
- * whose step counter, error and stop flag live in device memory - so the
- * steps of all running jobs overlap on the GPU. The host never waits for the
- * device inside a tick: progress is read from pinned status words.
- * A finished fit job's grid stays resident (for queries) until tg_release.
+ * and launches one training step of every running fit job:
+ *  - running jobs that share order and storage dtype are advanced together,
+ *    one launch per stage for all of them: one point-parallel kernel over the
+ *    concatenation of their fit batches (sampler, f and grad f, the L1 /
+ *    Eq. 7 / eikonal upstreams, the warp-aggregated coefficient gradient),
+ *    one Adam launch over all their coefficients, a device-gated evaluation
+ *    every eval_every steps and one thread per job for the step counter;
+ *  - a job with TG_FIT_DETERMINISTIC or a TV term runs alone on its own
+ *    stream as a CUDA graph captured at admission (sampler, binning, binned
+ *    forward, loss, binned backward, TV, Adam, gated evaluation).
+ * Step counters, errors and stop flags live in device memory; the host never
+ * waits for the device inside a tick and reads progress from pinned status
+ * words. A finished fit job's grid stays resident (for queries) until
+ * tg_release.
  * ------------------------------------------------------------------------ */
 typedef struct tg_server tg_server;
 typedef int64_t tg_job_id;
@@ -516,7 +523,16 @@ typedef struct {
     float lr, lambda_eik, init_std;
     float k_weight;             /* Eq. 7 adaptive weight (tg_sdf_step); <= 0: off */
     float lambda_tv;            /* total variation weight (tg_tv_step); 0: off */
+    int flags;                  /* TG_FIT_DETERMINISTIC | TG_FIT_LAZY_ADAM */
 } tg_fit_desc;
+
+/* tg_fit_desc.flags. TG_FIT_DETERMINISTIC: the job trains alone on its own
+ * stream with the bitwise-reproducible backward (TG_DETERMINISTIC) and an
+ * evaluation summed in a fixed order, so its grid is the same bits whatever
+ * else runs. TG_FIT_LAZY_ADAM: Adam as tg_adam_step_lazy (coefficients no
+ * point touched keep parameter and moments). */
+#define TG_FIT_DETERMINISTIC 1
+#define TG_FIT_LAZY_ADAM 2
 
 typedef enum {
     TG_JOB_QUEUED = 0,
@@ -548,7 +564,8 @@ TG_API tg_status tg_fit_job(tg_server *server, const tg_fit_desc *desc, tg_job_i
 
 /* Enqueue a query of N points (device, N x 3) against the grid of fit job
  * `grid_job` (queued, running or done but not released); out (device, N).
- * The query runs on the fit job's stream, between two of its steps. */
+ * The query runs on the stream that trains the grid (the job's own, or its
+ * group's), between two of its steps. */
 TG_API tg_status tg_query_job(tg_server *server, tg_job_id grid_job, const float *pts, int64_t N, float *out,
                               tg_job_id *id);
 

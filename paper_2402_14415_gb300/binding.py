@@ -52,7 +52,8 @@ class FitDesc(ctypes.Structure):
                 ("n_spheres", _int), ("n_boxes", _int), ("spheres", _vp), ("boxes", _vp), ("area_cdf", _vp),
                 ("points_per_step", _i64), ("eval_points", _i64), ("eval_every", _int), ("max_steps", _int),
                 ("tol", ctypes.c_float), ("lr", ctypes.c_float), ("lambda_eik", ctypes.c_float),
-                ("init_std", ctypes.c_float), ("k_weight", ctypes.c_float), ("lambda_tv", ctypes.c_float)]
+                ("init_std", ctypes.c_float), ("k_weight", ctypes.c_float), ("lambda_tv", ctypes.c_float),
+                ("flags", _int)]
 
 
 class JobResult(ctypes.Structure):
@@ -569,7 +570,7 @@ class Server:
 
     def fit_job(self, shape_spheres, shape_boxes, area_cdf, res, order=2, dtype="f32", seed=0, points_per_step=1 << 16,
                 eval_points=1 << 16, eval_every=10, max_steps=1000, tol=2e-3, lr=5e-3, lambda_eik=0.0,
-                init_std=1e-3, k_weight=0.0, lambda_tv=0.0) -> int:
+                init_std=1e-3, k_weight=0.0, lambda_tv=0.0, deterministic=False, lazy_adam=False) -> int:
         import numpy as np
         sph = np.ascontiguousarray(shape_spheres, np.float32).reshape(-1)
         box = np.ascontiguousarray(shape_boxes, np.float32).reshape(-1)
@@ -577,7 +578,7 @@ class Server:
         d = FitDesc(res, order, DTYPES[dtype] if isinstance(dtype, str) else dtype, seed, sph.size // 4, box.size // 6,
                     sph.ctypes.data if sph.size else None, box.ctypes.data if box.size else None, cdf.ctypes.data,
                     points_per_step, eval_points, eval_every, max_steps, tol, lr, lambda_eik, init_std, k_weight,
-                    lambda_tv)
+                    lambda_tv, (1 if deterministic else 0) | (2 if lazy_adam else 0))
         jid = _i64()
         _check(load().tg_fit_job(self._h, ctypes.byref(d), ctypes.byref(jid)), "tg_fit_job")
         return jid.value

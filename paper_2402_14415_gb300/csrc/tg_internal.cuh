@@ -137,9 +137,22 @@ __device__ __forceinline__ void red_block(float *p, const float *v)
         for (int i = 0; i < NV / 4; ++i)
             atomicAdd(reinterpret_cast<float4 *>(p) + i, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
     } else if constexpr (VW == 8) {
+        // an 8-byte-aligned block of 8k + 2 floats: 16-byte vector reductions from
+        // whichever of its first two elements is 16-byte aligned, and one 8-byte
+        // one for the remaining pair (K = 10: 3 reductions a vertex instead of 5)
+        if (reinterpret_cast<uintptr_t>(p) & 15) {
+            atomicAdd(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
 #pragma unroll
-        for (int i = 0; i < NV / 2; ++i)
-            atomicAdd(reinterpret_cast<float2 *>(p) + i, make_float2(v[2 * i], v[2 * i + 1]));
+            for (int i = 0; i < (NV - 2) / 4; ++i)
+                atomicAdd(reinterpret_cast<float4 *>(p + 2 + 4 * i),
+                          make_float4(v[2 + 4 * i], v[3 + 4 * i], v[4 + 4 * i], v[5 + 4 * i]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < (NV - 2) / 4; ++i)
+                atomicAdd(reinterpret_cast<float4 *>(p + 4 * i),
+                          make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+            atomicAdd(reinterpret_cast<float2 *>(p + NV - 2), make_float2(v[NV - 2], v[NV - 1]));
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < NV; ++i) atomicAdd(p + i, v[i]);

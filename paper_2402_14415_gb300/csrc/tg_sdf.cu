@@ -16,102 +16,22 @@ tg_status shape_view(const tg_shape *s, ShapeView *v, const char *who)
     return TG_OK;
 }
 
-// Signed distance of the union (Eq. 5): sphere |x - c| - r; box: distance to
-// the box surface, negative inside; union = minimum.
-__device__ __forceinline__ float sdf_union(const ShapeView &s, float x, float y, float z)
-{
-    float best = INFINITY;
-    for (int i = 0; i < s.ns; ++i) {
-        const float *q = s.sph + 4 * i;
-        const float dx = x - __ldg(q), dy = y - __ldg(q + 1), dz = z - __ldg(q + 2);
-        best = fminf(best, sqrtf(dx * dx + dy * dy + dz * dz) - __ldg(q + 3));
-    }
-    for (int i = 0; i < s.nb; ++i) {
-        const float *q = s.box + 6 * i;
-        const float ex = fabsf(x - __ldg(q)) - __ldg(q + 3);
-        const float ey = fabsf(y - __ldg(q + 1)) - __ldg(q + 4);
-        const float ez = fabsf(z - __ldg(q + 2)) - __ldg(q + 5);
-        const float ox = fmaxf(ex, 0.f), oy = fmaxf(ey, 0.f), oz = fmaxf(ez, 0.f);
-        const float d = sqrtf(ox * ox + oy * oy + oz * oz) + fminf(fmaxf(ex, fmaxf(ey, ez)), 0.f);
-        best = fminf(best, d);
-    }
-    return best;
-}
-
-__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
-
 __global__ void sdf_target_kernel(ShapeView s, const float *__restrict__ pts, int64_t N, float *__restrict__ d)
 {
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
         d[n] = sdf_union(s, clamp01(pts[3 * n]), clamp01(pts[3 * n + 1]), clamp01(pts[3 * n + 2]));
 }
 
-// An area-weighted surface point of one member from the uniforms u0, u1 (position),
-// u8 (member), u9 (box face).
-__device__ __forceinline__ void surface_candidate(const ShapeView &s, float u0, float u1, float u8, float u9, float *p)
-{
-    const int nm = s.ns + s.nb;
-    int prim = 0;
-    for (int i = 0; i < nm; ++i) prim += (__ldg(s.cdf + i) <= u8) ? 1 : 0;   // first entry > u8
-    prim = min(prim, nm - 1);
-    if (prim < s.ns) {
-        const float *q = s.sph + 4 * prim;
-        const float z = 1.f - 2.f * u0;
-        const float r = sqrtf(fmaxf(0.f, 1.f - z * z));
-        const float R = __ldg(q + 3);
-        p[0] = __ldg(q) + R * r * cospif(2.f * u1);
-        p[1] = __ldg(q + 1) + R * r * sinpif(2.f * u1);
-        p[2] = __ldg(q + 2) + R * z;
-    } else {
-        const float *q = s.box + 6 * (prim - s.ns);
-        const float c[3] = {__ldg(q), __ldg(q + 1), __ldg(q + 2)};
-        const float h[3] = {__ldg(q + 3), __ldg(q + 4), __ldg(q + 5)};
-        const float fa[3] = {h[1] * h[2], h[0] * h[2], h[0] * h[1]};
-        const float tot = 2.f * (fa[0] + fa[1] + fa[2]);
-        float run = 0.f;
-        int face = 0;
-        for (int f = 0; f < 6; ++f) {
-            run += fa[f / 2];
-            face += (run / tot <= u9) ? 1 : 0;
-        }
-        face = min(face, 5);
-        const int ax = face / 2, a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
-        p[ax] = c[ax] + ((face % 2 == 0) ? -h[ax] : h[ax]);
-        p[a1] = c[a1] + (2.f * u0 - 1.f) * h[a1];
-        p[a2] = c[a2] + (2.f * u1 - 1.f) * h[a2];
-    }
-}
-
 __global__ void sdf_sample_kernel(ShapeView s, uint64_t seed, int64_t step, const int64_t *__restrict__ step_dev,
                                   int64_t N, float jitter, float *__restrict__ pts)
 {
-    constexpr uint64_t SLOTS = 16;
     if (step_dev) step = *step_dev;
-    const int64_t n_uni = N / 2;
-    const uint64_t base = (uint64_t)step * 256ull;
-    const uint64_t key_u = stream_key(seed, base + 255ull);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t b = (uint64_t)j * SLOTS;
-        float p[3] = {uniform_k(key_u, b), uniform_k(key_u, b + 1), uniform_k(key_u, b + 2)};
-        if (j >= n_uni) {
-            for (int a = 0; a < 8; ++a) {
-                const uint64_t key = stream_key(seed, base + (uint64_t)a);
-                float cand[3];
-                surface_candidate(s, uniform_k(key, b), uniform_k(key, b + 1), uniform_k(key, b + 8),
-                                  uniform_k(key, b + 9), cand);
-                if (sdf_union(s, cand[0], cand[1], cand[2]) > -1e-6f) {
-                    p[0] = cand[0]; p[1] = cand[1]; p[2] = cand[2];
-                    break;
-                }
-            }
-            if (jitter > 0.f) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) p[k] += jitter * normal_k(key_u, (uint64_t)j * (SLOTS / 2) + 2 + k);
-            }
-        }
-        pts[3 * j] = clamp01(p[0]);
-        pts[3 * j + 1] = clamp01(p[1]);
-        pts[3 * j + 2] = clamp01(p[2]);
+        float p[3];
+        sample_sdf_point(s, seed, step, N, j, jitter, p);
+        pts[3 * j] = p[0];
+        pts[3 * j + 1] = p[1];
+        pts[3 * j + 2] = p[2];
     }
 }
 
@@ -129,8 +49,8 @@ __device__ __forceinline__ float block_sum(float v, float *tmp)
     return s;
 }
 
-// Per-point loss in binned order: r = f - d(x), dL/df = sign(r) / N and, with
-// an eikonal weight, dL/d(grad_x f) = lambda 2 (|g| - 1) g / |g| / N.
+// Per-point loss in binned order (sdf_point_upstream): the upstreams of the
+// L1 term with Eq. 7's weight and of the eikonal term, and the block's loss sums.
 __global__ void __launch_bounds__(256)
 sdf_loss_kernel(ShapeView s, const float4 *__restrict__ sorted, int64_t N, const float *__restrict__ f,
                 const float *__restrict__ g, float lambda, float k_weight, float inv_n, float *__restrict__ uf,
@@ -141,24 +61,15 @@ sdf_loss_kernel(ShapeView s, const float4 *__restrict__ sorted, int64_t N, const
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
         const float4 q = sorted[p];
         const float d = sdf_union(s, clamp01(q.x), clamp01(q.y), clamp01(q.z));
-        const float r = f[p] - d;
-        // Eq. 7: w = max(w'(f), w'(d)), w'(z) = 1 - |2 sigmoid(k z) - 1| = 2 e / (1 + e), e = exp(-|k z|);
-        // a fixed weight of the residual (k <= 0: w = 1)
-        float w = 1.f;
-        if (k_weight > 0.f) {
-            const float ef = expf(-fabsf(k_weight * f[p])), ed = expf(-fabsf(k_weight * d));
-            w = fmaxf(2.f * ef / (1.f + ef), 2.f * ed / (1.f + ed));
-        }
-        l1 += w * fabsf(r);
-        uf[p] = r > 0.f ? w * inv_n : (r < 0.f ? -w * inv_n : 0.f);
+        float gp[3], u[3], a, e;
+        if (g) { gp[0] = g[3 * p]; gp[1] = g[3 * p + 1]; gp[2] = g[3 * p + 2]; }
+        sdf_point_upstream(f[p], g ? gp : nullptr, d, lambda, k_weight, inv_n, uf + p, u, &a, &e);
+        l1 += a;
+        eik += e;
         if (g) {
-            const float gx = g[3 * p], gy = g[3 * p + 1], gz = g[3 * p + 2];
-            const float e = sqrtf(gx * gx + gy * gy + gz * gz);
-            eik += (e - 1.f) * (e - 1.f);
-            const float c = e < 1e-12f ? 0.f : lambda * 2.f * (e - 1.f) / e * inv_n;
-            ug[3 * p] = c * gx;
-            ug[3 * p + 1] = c * gy;
-            ug[3 * p + 2] = c * gz;
+            ug[3 * p] = u[0];
+            ug[3 * p + 1] = u[1];
+            ug[3 * p + 2] = u[2];
         }
     }
     const float a = block_sum(l1, tmp);
@@ -174,7 +85,8 @@ sdf_loss_kernel(ShapeView s, const float4 *__restrict__ sorted, int64_t N, const
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256)
 sdf_error_kernel(ShapeView s, const T *__restrict__ coefs, int res, const float *__restrict__ pts, int64_t N,
-                 float *__restrict__ err, const int *__restrict__ gate, unsigned long long *__restrict__ iou)
+                 float *__restrict__ err, const int *__restrict__ gate, unsigned long long *__restrict__ iou,
+                 float *__restrict__ partials)
 {
     if (gate && *gate == 0) return;
     __shared__ float tmp[32];
@@ -201,9 +113,12 @@ sdf_error_kernel(ShapeView s, const T *__restrict__ coefs, int res, const float 
         inter += (f < 0.f && d < 0.f);
         uni += (f < 0.f || d < 0.f);
     }
-    if (err) {
+    if (err || partials) {
         const float a = block_sum(acc, tmp);
-        if (threadIdx.x == 0) atomicAdd(err, a);
+        if (threadIdx.x == 0) {
+            if (partials) partials[blockIdx.x] = a;     // summed in block order by sum_partials_kernel
+            else atomicAdd(err, a);
+        }
     }
     if (iou) {
 #pragma unroll
@@ -226,7 +141,7 @@ static unsigned blocks_for(int64_t n, int per_sm = 8)
 
 tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, const float *pts, int64_t N,
                         uint64_t seed, int64_t step, const int64_t *step_dev, float lambda_eik, float k_weight,
-                        float *coef_grad, float *loss_sums, cudaStream_t cs)
+                        float *coef_grad, float *loss_sums, cudaStream_t cs, bool deterministic)
 {
     tg_status st;
     if ((st = ensure_stage(bt, 11 * N, "tg_sdf_step")) != TG_OK) return st;
@@ -243,15 +158,29 @@ tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, cons
     sdf_loss_kernel<<<blocks_for(N), 256, 0, cs>>>(s, bt->sorted, N, f, eik ? gx : nullptr, lambda_eik, k_weight,
                                                    1.0f / (float)N, uf, ug, loss_sums);
     if ((st = launch_status("tg_sdf_step: loss")) != TG_OK) return st;
-    return tg_query_backward_binned(g, bt, uf, eik ? ug : nullptr, coef_grad, TG_ORDER_BINNED, cs);
+    return tg_query_backward_binned(g, bt, uf, eik ? ug : nullptr, coef_grad,
+                                    TG_ORDER_BINNED | (deterministic ? TG_DETERMINISTIC : 0), cs);
 }
 
+// The per-block sums of sdf_error_kernel added in block order (a fixed order, so the
+// evaluated error does not depend on which block finished first).
+__global__ void sum_partials_kernel(const float *__restrict__ partials, int n, float *__restrict__ err,
+                                    const int *__restrict__ gate)
+{
+    if (gate && *gate == 0) return;
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += partials[i];
+    *err += s;
+}
+
+int error_blocks(int64_t N) { return (int)blocks_for(N); }
+
 tg_status sdf_error_impl(const tg_grid *g, const ShapeView &s, const float *pts, int64_t N, float *err_sum,
-                         const int *gate, cudaStream_t cs, unsigned long long *iou)
+                         const int *gate, cudaStream_t cs, unsigned long long *iou, float *partials)
 {
     const unsigned nb = blocks_for(N);
 #define TG_ERR(T, O) \
-    sdf_error_kernel<T, O><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, pts, N, err_sum, gate, iou)
+    sdf_error_kernel<T, O><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, pts, N, err_sum, gate, iou, partials)
     if (g->dtype == TG_F32) {
         if (g->order == 0) TG_ERR(float, 0); else if (g->order == 1) TG_ERR(float, 1); else TG_ERR(float, 2);
     } else if (g->dtype == TG_BF16) {
@@ -260,7 +189,10 @@ tg_status sdf_error_impl(const tg_grid *g, const ShapeView &s, const float *pts,
         if (g->order == 0) TG_ERR(__half, 0); else if (g->order == 1) TG_ERR(__half, 1); else TG_ERR(__half, 2);
     }
 #undef TG_ERR
-    return launch_status("tg_sdf_error");
+    tg_status st = launch_status("tg_sdf_error");
+    if (st != TG_OK || !partials) return st;
+    sum_partials_kernel<<<1, 1, 0, cs>>>(partials, (int)nb, err_sum, gate);
+    return launch_status("tg_sdf_error: ordered sum");
 }
 
 }  // namespace tg
@@ -309,7 +241,7 @@ tg_status tg_sdf_step(const tg_grid *g, tg_batch *bt, const tg_shape *shape, con
     if (!pts && !s.cdf) return fail(TG_EINVAL, "tg_sdf_step: sampling needs area_cdf");
     if (!(lambda_eik >= 0.f)) return fail(TG_EINVAL, "tg_sdf_step: lambda_eik must be >= 0");
     return sdf_step_impl(g, bt, s, pts, N, seed, step, nullptr, lambda_eik, k_weight, coef_grad, loss_sums,
-                         (cudaStream_t)stream);
+                         (cudaStream_t)stream, false);
 }
 
 tg_status tg_sdf_error(const tg_grid *g, const tg_shape *shape, const float *pts, int64_t N, float *err_sum,

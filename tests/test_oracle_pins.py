@@ -612,6 +612,24 @@ def test_render_gradient_finite_differences():
         assert abs(fd - cg[j]) < 1e-7 + 1e-5 * abs(fd), ("colour", j, fd, cg[j])
 
 
+def test_render_term_magnitudes_bound_the_gradient():
+    """The per-coefficient sums of term magnitudes (want_abs) bound the gradients, vanish where a coefficient
+    receives nothing, and equal |gradient| where every term is positive: an order-0 colour grid against a zero
+    target (C - 0 > 0, T alpha > 0, sigmoid' > 0, corner weights >= 0)."""
+    r = rng(91)
+    res = 3
+    o, d = W.random_rays(6, 4, radius=1.2, spread=0.3)
+    for od, oc, tgt in ((2, 1, r.random((4, 3)).astype(np.float32)), (1, 0, np.zeros((4, 3), np.float32))):
+        dco = r.normal(size=res ** 3 * oracle.num_coefs(3, od)) * 0.5
+        cco = r.normal(size=res ** 3 * 3 * oracle.num_coefs(3, oc)) * 0.5
+        _, _, dg, cg, da, ca = oracle.render(res, od, dco, oc, cco, o, d, 10, seed=4, target=tgt, want_abs=True)
+        assert (da >= np.abs(dg) * (1 - 1e-12)).all() and (ca >= np.abs(cg) * (1 - 1e-12)).all()
+        assert (dg[da == 0] == 0).all() and (cg[ca == 0] == 0).all()
+        assert (ca > 0).any() and (da > 0).any()
+        if oc == 0:
+            np.testing.assert_allclose(ca, np.abs(cg), rtol=1e-12, atol=0)
+
+
 def test_blob_scene_renderer_limits():
     """A dense blob saturates to its colour; a ray that misses the cube renders bg; an empty scene is bg."""
     mu = np.array([[0.5, 0.5, 0.5]]); icov = np.eye(3)[None] / 0.05 ** 2
