@@ -343,9 +343,14 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(world, e0.elapsed_time(e1)) / args.steps
     barrier(world)
-    tg.tg_batch_bin(batch, P)                      # the headline's f (the input-order pass ran last)
-    tg.tg_query_binned(g, batch, out=out, binned_order=True)
-    assert torch.equal(outs_h[(1 + args.steps) % 2], out.cpu()), "end-to-end f differs from the device-timed f"
+    # the order of points inside a brick differs between binnings (shared-memory ranks), so the last
+    # end-to-end f is taken back to input order with that step's own permutation before the comparison
+    perm = tg.tg_batch_order(batch).long().cpu()
+    f_e2e = torch.empty_like(outs_h[0])
+    f_e2e[perm] = outs_h[(1 + args.steps) % 2]
+    tg.tg_batch_bin(batch, P)
+    tg.tg_query_binned(g, batch, out=out)
+    assert torch.equal(f_e2e, out.cpu()), "end-to-end f differs from the device-timed f"
 
     hbm, peak_kind = peaks()
     fwd_bytes, bwd_bytes = algorithmic_bytes(N, RES ** 3)
@@ -944,10 +949,30 @@ def profile_render():
     print("profile render pass done")
 
 
+def profile_serve(steps=3):
+    """Six SDF fit jobs of one group (order 2, FP32, res 64 / 96, 2^16 points per step) through the server for a
+    few steps, for ncu captures of the batched step's kernels."""
+    import torch
+
+    import paper_2402_14415_gb300 as tg
+    import workloads as W
+    srv = tg.Server(budget_bytes=16 << 30, max_running=16)
+    ids = []
+    for k in range(6):
+        sh = W.union_shape(300 + k)
+        ids.append(srv.fit_job(sh.spheres, sh.boxes, sh.area_cdf(), res=64 + 32 * (k % 2), order=2, dtype="f32",
+                               seed=300 + k, points_per_step=1 << 16, eval_points=1 << 14, eval_every=10,
+                               max_steps=steps, tol=0.0, lr=5e-3))
+    srv.run_until_idle(timeout_s=60)
+    torch.cuda.synchronize()
+    print("profile serve pass done:", [srv.poll(j)["steps"] for j in ids])
+    srv.close()
+
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # full-size launches (binned order) captured by `ncu ... python bench.py --profile`
 # (profiles/query_step_256_o2_2e24_full.md); None once the kernel has changed since.
-TRAFFIC = {"forward": None, "backward": None, "bin": None}
+TRAFFIC = {"forward": 0.939709696e9 + 0.064290304e9, "backward": 1.006815e9 + 0.612811264e9, "bin": None}
 KERNEL_NAMES = {"bin": "bin_* (5 kernels, tg_batch_bin)", "forward": "brick_fwd_kernel (tg_query_binned)",
                 "backward": "brick_bwd_fast_kernel (tg_query_backward_binned)"}
 
@@ -968,6 +993,8 @@ def main():
                     help="run three SDF fit steps at 256^3 order 2 in this storage dtype (for ncu captures)")
     ap.add_argument("--profile-render", action="store_true",
                     help="run three ray-march training steps at 160^3 (for ncu captures)")
+    ap.add_argument("--profile-serve", action="store_true",
+                    help="run six fit jobs of one group through the server for three steps (for ncu captures)")
     ap.add_argument("--cpu-baseline-from", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_baseline_from:
@@ -979,6 +1006,8 @@ def main():
         return profile_fit(args.profile_fit)
     if args.profile_render:
         return profile_render()
+    if args.profile_serve:
+        return profile_serve()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)

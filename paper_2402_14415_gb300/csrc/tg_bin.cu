@@ -226,21 +226,26 @@ bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk,
     const int64_t lo = (int64_t)blockIdx.x * chunk;
     const int64_t hi = min(N, lo + chunk);
     constexpr int U = kCoarseTile / kHistThreads;
+    // the next tile's points are loaded while this one is ranked, staged and written
+    float x[U][3], xn[U][3];
+    if (lo < hi) {
+        const int cnt0 = (int)min((int64_t)kCoarseTile, hi - lo);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * kHistThreads;
+            if (i < cnt0) load_point3(pts, lo + i, x[u]);
+        }
+    }
     for (int64_t t0 = lo; t0 < hi; t0 += kCoarseTile) {
         const int cnt = (int)min((int64_t)kCoarseTile, hi - t0);
+        const int cnt1 = (int)max((int64_t)0, min((int64_t)kCoarseTile, hi - (t0 + kCoarseTile)));
         for (int j = threadIdx.x; j < ncoarse; j += blockDim.x) S.cnt[j] = 0;
         __syncthreads();
-        float x[U][3];
         int key[U], rank[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = threadIdx.x + u * kHistThreads;
             key[u] = -1;
-            if (i < cnt) load_point3(pts, t0 + i, x[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = threadIdx.x + u * kHistThreads;
             if (i < cnt) {
                 int c[3];
                 float t[3];
@@ -248,6 +253,11 @@ bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk,
                 key[u] = brick_of(c, nbx, nby) / kCoarse;
                 rank[u] = atomicAdd(S.cnt + key[u], 1);
             }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * kHistThreads;
+            if (i < cnt1) load_point3(pts, t0 + kCoarseTile + i, xn[u]);
         }
         __syncthreads();
         {   // tile offsets per bin, and one run per bin reserved from the chunk's cursor
@@ -274,6 +284,12 @@ bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk,
             const int bkey = S.bin[q];
             coarse[S.gbase[bkey] + (q - S.loff[bkey])] = S.stage[q];
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            x[u][0] = xn[u][0];
+            x[u][1] = xn[u][1];
+            x[u][2] = xn[u][2];
+        }
         __syncthreads();
     }
 }
@@ -293,21 +309,26 @@ bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int n
     const float scale = (float)(res - 1);
     constexpr int U = kFineTile / kFineThreads;
     const int lane = threadIdx.x & 31;
+    // the next tile's records are loaded while this one is ranked, staged and written
+    float4 q[U], qn[U];
+    if (lo < hi) {
+        const int cnt0 = min(kFineTile, hi - lo);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * kFineThreads;
+            if (i < cnt0) q[u] = coarse[lo + i];
+        }
+    }
     for (int t0 = lo; t0 < hi; t0 += kFineTile) {
         const int cnt = min(kFineTile, hi - t0);
+        const int cnt1 = max(0, min(kFineTile, hi - (t0 + kFineTile)));
         for (int j = threadIdx.x; j < kCoarse; j += blockDim.x) S.cnt[j] = 0;
         __syncthreads();
-        float4 q[U];
         int key[U], rank[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = threadIdx.x + u * kFineThreads;
             key[u] = -1;
-            if (i < cnt) q[u] = coarse[t0 + i];
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = threadIdx.x + u * kFineThreads;
             if (i < cnt) {
                 const float x[3] = {q[u].x, q[u].y, q[u].z};
                 int c[3];
@@ -316,6 +337,11 @@ bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int n
                 key[u] = brick_of(c, nbx, nby) - b0;
                 rank[u] = atomicAdd(S.cnt + key[u], 1);
             }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = threadIdx.x + u * kFineThreads;
+            if (i < cnt1) qn[u] = coarse[t0 + kFineTile + i];
         }
         __syncthreads();
         if (threadIdx.x < 32) {   // one warp: offsets of the 64 bricks in the tile, and their runs
@@ -350,6 +376,8 @@ bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int n
             sorted[slot] = r;
             perm[slot] = __float_as_int(r.w);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = qn[u];
         __syncthreads();
     }
 }

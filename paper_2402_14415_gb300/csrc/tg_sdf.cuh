@@ -65,10 +65,15 @@ __device__ __forceinline__ void surface_candidate(const ShapeView &s, float u0, 
             face += (run / tot <= u9) ? 1 : 0;
         }
         face = min(face, 5);
-        const int ax = face / 2, a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
-        p[ax] = c[ax] + ((face % 2 == 0) ? -h[ax] : h[ax]);
-        p[a1] = c[a1] + (2.f * u0 - 1.f) * h[a1];
-        p[a2] = c[a2] + (2.f * u1 - 1.f) * h[a2];
+        const int ax = face / 2, a1 = (ax + 1) % 3;
+        // axis ax is the face's normal, a1 takes u0 and the third axis u1; the
+        // roles are selected per component so that every array index is a constant
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float along = k == ax ? ((face % 2 == 0) ? -h[k] : h[k])
+                                        : (k == a1 ? (2.f * u0 - 1.f) * h[k] : (2.f * u1 - 1.f) * h[k]);
+            p[k] = c[k] + along;
+        }
     }
 }
 

@@ -37,7 +37,11 @@ struct BatchJob {
     uint64_t seed;
     int64_t ncoef;
     int64_t pbase, npts;     // the job's points in the batch: [pbase, pbase + npts)
-    int64_t gbase;           // its first float4 group in the Adam pass (ceil(ncoef / 4) groups)
+    int64_t gbase;           // its first unit of the Adam pass: ceil(ncoef / 4) float4 groups, or, with
+                             // touched flags, ceil(nv / 4) runs of 4 vertices
+    unsigned char *touched;  // lazy Adam: one flag per vertex, set by the fit kernel, cleared by Adam; or null
+    int64_t nv;              // vertices (ncoef = nv * K)
+    int K;
     int64_t n_eval;
     int res, eval_every, max_steps, lazy;
     float lambda_eik, k_weight, lr, tol;

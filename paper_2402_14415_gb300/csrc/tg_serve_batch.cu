@@ -7,7 +7,11 @@
 // job's grid (Eq. 2 - Eq. 4), forms the loss upstreams (Eq. 6 with Eq. 7's
 // weight, the eikonal term of Eq. 8) and scatters the coefficient gradient
 // with warp-aggregated vector reductions into the job's gradient. One Adam
-// launch covers the float4 groups of all jobs' coefficients, a gated launch
+// launch covers the float4 groups of all jobs' coefficients; a lazy-Adam job
+// instead has the fit kernel flag every vertex its points reach, and Adam
+// visits the flagged vertices only (an unflagged vertex has a zero gradient,
+// which lazy Adam leaves alone), so its cost follows the points, not the grid
+// size. A gated launch
 // evaluates the jobs whose evaluation step it is, and one thread per job
 // keeps the step counter and status.
 #include "tg_adam.cuh"
@@ -72,7 +76,7 @@ __global__ void batch_prologue_kernel(const BatchJob *__restrict__ jobs, int n)
 }
 
 template <typename T, int ORDER>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 batch_fit_kernel(const BatchJob *__restrict__ jobs, int njobs, int64_t total)
 {
     constexpr int K = Basis<3, ORDER>::K;
@@ -107,6 +111,10 @@ batch_fit_kernel(const BatchJob *__restrict__ jobs, int njobs, int64_t total)
         const int max_group = __reduce_max_sync(valid, (unsigned)group);
         const bool leader = (__ffs(peers) - 1) == lane;
         float *grad = J.grad;
+        if (J.touched) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) J.touched[v0 + corner_offset<3>(i, res)] = 1;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float ctr[K];
@@ -127,7 +135,8 @@ batch_fit_kernel(const BatchJob *__restrict__ jobs, int njobs, int64_t total)
     }
 }
 
-// Adam over the float4 groups of every job (a group past a job's end is handled element by element).
+// Adam over the units of every job: float4 groups (a group past a job's end is handled element by element), or
+// runs of 4 vertices of a job with touched flags.
 template <typename T, typename M>
 __global__ void __launch_bounds__(256)
 batch_adam_kernel(const BatchJob *__restrict__ jobs, int njobs, int64_t total_groups)
@@ -143,6 +152,33 @@ batch_adam_kernel(const BatchJob *__restrict__ jobs, int njobs, int64_t total_gr
         M *m = (M *)J.m, *v = (M *)J.v;
         T *shadow = (T *)J.shadow;
         const bool lazy = J.lazy != 0;
+        if (J.touched) {      // 4 vertices per unit; only the flagged ones are read
+            const int64_t v0 = 4 * k;
+            const int nvu = (int)min((int64_t)4, J.nv - v0);
+            unsigned fl = 0u;
+            if (nvu == 4) fl = *reinterpret_cast<const unsigned *>(J.touched + v0);
+            else
+                for (int i = 0; i < nvu; ++i) fl |= (unsigned)J.touched[v0 + i] << (8 * i);
+            if (fl == 0u) continue;
+            for (int i = 0; i < nvu; ++i) {
+                if (((fl >> (8 * i)) & 0xffu) == 0u) continue;
+                for (int64_t e = (v0 + i) * J.K; e < (v0 + i + 1) * J.K; ++e) {
+                    const float ge = g[e];
+                    if (ge == 0.f) continue;
+                    float pp = p[e], mm = Moments<M>::get(m, e), vv = Moments<M>::get(v, e);
+                    adam_one(pp, ge, mm, vv, a);
+                    p[e] = pp;
+                    Moments<M>::put(m, e, mm);
+                    Moments<M>::put(v, e, vv);
+                    g[e] = 0.0f;
+                    if (shadow) shadow[e] = from_f32<T>(pp);
+                }
+            }
+            if (nvu == 4) *reinterpret_cast<unsigned *>(J.touched + v0) = 0u;
+            else
+                for (int i = 0; i < nvu; ++i) J.touched[v0 + i] = 0;
+            continue;
+        }
         if (4 * k + 3 < J.ncoef) {
             const float4 gg = __ldcs(reinterpret_cast<float4 *>(g) + k);
             if (lazy && gg.x == 0.f && gg.y == 0.f && gg.z == 0.f && gg.w == 0.f) continue;
@@ -233,7 +269,7 @@ static tg_status batch_launch(const BatchJob *host, BatchJob *dev, int n, DevSta
 {
     const BatchJob &last = host[n - 1];
     const int64_t total = last.pbase + last.npts;
-    const int64_t groups = last.gbase + (last.ncoef + 3) / 4;
+    const int64_t groups = last.gbase + (last.touched ? (last.nv + 3) / 4 : (last.ncoef + 3) / 4);
     int64_t max_eval = 0;
     for (int j = 0; j < n; ++j) max_eval = host[j].n_eval > max_eval ? host[j].n_eval : max_eval;
     const int64_t cap = (int64_t)num_sms() * 8;

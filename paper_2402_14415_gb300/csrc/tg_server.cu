@@ -77,6 +77,7 @@ struct Job {
     int64_t qn = 0;
 
     float *partials = nullptr;       // deterministic evaluation: per-block error sums
+    unsigned char *touched = nullptr;   // batched lazy-Adam job: one flag per vertex
     bool batched = false;            // advanced with its group (no own stream or graph)
     int group = -1;                  // group key of a batched job
 
@@ -136,8 +137,9 @@ static size_t fit_bytes(const tg_fit_desc &d)
 {
     const int K = num_coefs(3, d.order);
     const size_t ncoef = (size_t)d.res * d.res * d.res * K;
-    if (!runs_alone(d))    // batched: the grid, Adam state, gradient, evaluation points and status block
-        return (d.dtype == TG_F32 ? ncoef * (4 + 8 + 4) : ncoef * (4 + 4 + 4 + 2)) + (size_t)d.eval_points * 12 + 4096;
+    if (!runs_alone(d))    // batched: the grid, Adam state, gradient, evaluation points, status block, touched flags
+        return (d.dtype == TG_F32 ? ncoef * (4 + 8 + 4) : ncoef * (4 + 4 + 4 + 2)) + (size_t)d.eval_points * 12 + 4096 +
+               ((d.flags & TG_FIT_LAZY_ADAM) ? ncoef / K + 16 : 0);     // flags: an upper bound
     // master, Adam m + v (FP32, or BF16 for BF16 / FP16 storage), gradient, shadow
     size_t b = d.dtype == TG_F32 ? ncoef * (4 + 8 + 4) : ncoef * (4 + 4 + 4 + 2);
     const size_t nb = (size_t)((d.res - 2) / 8 + 1);
@@ -159,6 +161,7 @@ static void free_fit_scratch(Job *j)
     cudaFree(j->eval_pts); j->eval_pts = nullptr;
     cudaFree(j->small); j->small = nullptr;
     cudaFree(j->partials); j->partials = nullptr;
+    cudaFree(j->touched); j->touched = nullptr;
 }
 
 static void free_job(Job *j)
@@ -219,6 +222,11 @@ static tg_status admit_fit(Job *j, cudaStream_t group_stream)
     if (st == TG_OK) st = ensure_adam_state(j->grid);
     if (st == TG_OK) st = dev_alloc((void **)&j->grad, (size_t)j->grid->ncoef * 4 + 16, "server: gradient");
     if (st == TG_OK) st = dev_alloc((void **)&j->small, 64, "server: status block");
+    // touched flags where a step reaches few of the vertices (8 corners a point against at least 16 vertices
+    // a point): Adam then visits the flagged vertices only; on denser grids it streams every coefficient
+    const bool flags = !alone && (d.flags & TG_FIT_LAZY_ADAM) && j->grid->nv >= 16 * d.points_per_step;
+    if (st == TG_OK && flags)
+        st = dev_alloc((void **)&j->touched, (size_t)j->grid->nv + 16, "server: touched flags");
     const size_t nsh = j->sph.size() + j->box.size() + j->cdf.size();
     if (st == TG_OK) st = dev_alloc((void **)&j->shape_dev, nsh * 4, "server: shape");
     if (st == TG_OK) st = dev_alloc((void **)&j->eval_pts, (size_t)d.eval_points * 12, "server: eval points");
@@ -226,6 +234,8 @@ static tg_status admit_fit(Job *j, cudaStream_t group_stream)
     cudaStream_t s = alone ? j->stream : group_stream;
     st = cuda_status(cudaMemsetAsync(j->grad, 0, (size_t)j->grid->ncoef * 4, s), "server: zero gradient");
     if (st == TG_OK) st = cuda_status(cudaMemsetAsync(j->small, 0, 64, s), "server: zero status");
+    if (st == TG_OK && flags)
+        st = cuda_status(cudaMemsetAsync(j->touched, 0, (size_t)j->grid->nv + 16, s), "server: zero flags");
     float *sp = j->shape_dev, *bp = sp + j->sph.size(), *cp = bp + j->box.size();
     if (st == TG_OK && !j->sph.empty())
         st = cuda_status(cudaMemcpyAsync(sp, j->sph.data(), j->sph.size() * 4, cudaMemcpyHostToDevice, s), "server: shape");
@@ -573,6 +583,9 @@ tg_status tg_server_step(tg_server *s, int *pending)
             b.pbase = pbase;
             b.npts = d.points_per_step;
             b.gbase = gbase;
+            b.touched = j->touched;
+            b.nv = j->grid->nv;
+            b.K = j->grid->K;
             b.n_eval = d.eval_points;
             b.res = d.res;
             b.eval_every = d.eval_every;
@@ -583,7 +596,7 @@ tg_status tg_server_step(tg_server *s, int *pending)
             b.lr = d.lr;
             b.tol = d.tol;
             pbase += d.points_per_step;
-            gbase += (j->grid->ncoef + 3) / 4;
+            gbase += j->touched ? (j->grid->nv + 3) / 4 : (j->grid->ncoef + 3) / 4;
         }
         if (st == TG_OK) st = batch_step(g->table_host, g->table_dev, (int)mem.size(), g->order, g->dtype, g->status_dev,
                                          g->stream);
