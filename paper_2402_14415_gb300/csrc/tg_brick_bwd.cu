@@ -12,6 +12,7 @@
 #include <stdlib.h>
 
 #include "tg_bwd_fast.cuh"
+#include "tg_records.cuh"
 
 namespace tg {
 
@@ -300,6 +301,19 @@ static tg_status binned_bwd(const tg_grid *g, const tg_batch *bt, const float *u
     if constexpr (DIM != 3) {
         return fail(TG_EINVAL, "binned path is 3-D only");
     } else {
+        constexpr int NVr = Basis<3, ORDER>::K * C;
+        const bool tma_ok = brick_tma_ok(g->res, NVr, 4, BoxInner<float, NVr>::value, grad);
+        if (!det && use_records_path(bt->n, bt->nbricks, ug != nullptr, tma_ok)) {   // few points per brick
+            // (or rows TMA cannot move): one thread per record
+            const unsigned blocks = records_blocks(bt->n);
+            if (in_order)
+                records_bwd_kernel<ORDER, C, true><<<blocks, kQueryThreads, 0, s>>>(g->res, bt->sorted, bt->n, uf, ug,
+                                                                                    grad);
+            else
+                records_bwd_kernel<ORDER, C, false><<<blocks, kQueryThreads, 0, s>>>(g->res, bt->sorted, bt->n, uf, ug,
+                                                                                     grad);
+            return launch_status("tg_query_backward_binned");
+        }
         constexpr int NV = Basis<3, ORDER>::K * C;
         CUtensorMap map;
         tg_status st = make_brick_map(&map, grad, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->res, NV,

@@ -7,6 +7,7 @@
 // coefficient and corner). Outputs go straight to the caller's order: the
 // binned slot, or the input index that every binned record carries.
 #include "tg_gather.cuh"
+#include "tg_records.cuh"
 
 namespace tg {
 
@@ -207,6 +208,20 @@ struct BinnedFwd {
         if constexpr (DIM != 3) {
             return fail(TG_EINVAL, "binned path is 3-D only");
         } else {
+            constexpr int NVr = Basis<3, ORDER>::K * C;
+            const bool tma_ok = brick_tma_ok(g->res, NVr, (int)sizeof(T), BoxInner<T, NVr>::value, g->store);
+            if (use_records_path(bt->n, bt->nbricks, gx != nullptr, tma_ok)) {   // few points per brick
+                // (or rows TMA cannot move): one thread per record
+                const T *coefs = reinterpret_cast<const T *>(g->store);
+                const unsigned blocks = records_blocks(bt->n);
+                if (in_order)
+                    records_fwd_kernel<T, ORDER, C, true><<<blocks, kQueryThreads, 0, s>>>(coefs, g->res, bt->sorted,
+                                                                                           bt->n, out, gx);
+                else
+                    records_fwd_kernel<T, ORDER, C, false><<<blocks, kQueryThreads, 0, s>>>(coefs, g->res, bt->sorted,
+                                                                                            bt->n, out, gx);
+                return launch_status("tg_query_binned");
+            }
             constexpr int NV = Basis<3, ORDER>::K * C;
             CUtensorMap map;
             const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32

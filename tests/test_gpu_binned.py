@@ -23,8 +23,17 @@ def clustered(n, seed=3):
     return np.concatenate([c[k] + 0.01 * r.standard_normal((n // 4, 3)) for k in range(4)]).astype(np.float32)
 
 
+@pytest.fixture(params=["auto", "brick", "records"])
+def binned_path(request, monkeypatch):
+    """The binned passes take the brick kernels or, for batches with few points per brick, one thread per record;
+    TG_BINNED_PATH forces either (read by the library at every call)."""
+    if request.param != "auto":
+        monkeypatch.setenv("TG_BINNED_PATH", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("res,order,C,dtype", SHAPES)
-def test_binned_forward_backward_parity(tg, res, order, C, dtype):
+def test_binned_forward_backward_parity(tg, res, order, C, dtype, binned_path):
     coefs = W.init_coefs(3, res, order, C, seed=1, std=0.5)
     g = tg.tg_create(3, res, order, C, dtype)
     tg.tg_set_coefs(g, to_dev(coefs))
@@ -50,7 +59,7 @@ def test_binned_forward_backward_parity(tg, res, order, C, dtype):
 
 
 @pytest.mark.parametrize("C,order", [(1, 2), (3, 1)])
-def test_binned_order_io(tg, C, order):
+def test_binned_order_io(tg, C, order, binned_path):
     """TG_ORDER_BINNED outputs/upstreams equal the input-order ones through the batch permutation."""
     res = 26
     coefs = W.init_coefs(3, res, order, C, seed=2, std=0.4)
@@ -127,12 +136,30 @@ def test_binned_empty_batch(tg):
     assert out.shape == (0, 1)
 
 
+def test_binned_rows_tma_cannot_move(tg):
+    """11 x 40-byte rows are not whole 16-byte units, so no brick tile can be moved by TMA: the binned passes take
+    the per-record path (equal to the point-parallel query), and the deterministic backward, which needs the
+    brick kernels, is refused."""
+    g = tg.tg_create(3, 11, 2, 1, "f32", seed=3, init_std=0.5)
+    P = torch.rand((5000, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(4))
+    batch = tg.tg_batch_create(3, 11, 5000)
+    tg.tg_batch_bin(batch, P)
+    out, gx = tg.tg_query_binned(g, batch, want_grad=True)
+    out_p, gx_p = tg.tg_query(g, P, want_grad=True)
+    assert torch.equal(out, out_p) and torch.equal(gx, gx_p)
+    U = torch.randn((5000, 1), device="cuda")
+    grad_b = torch.zeros(g.n_coefs, device="cuda")
+    grad_p = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward_binned(g, batch, U, grad_b)
+    tg.tg_query_backward(g, P, U, grad_p)
+    torch.testing.assert_close(grad_b, grad_p, rtol=1e-4, atol=1e-5)
+    with pytest.raises(tg.TGError):
+        tg.tg_query_backward_binned(g, batch, U, grad_b, deterministic=True)
+
+
 def test_binned_rejects_unsupported(tg):
-    g = tg.tg_create(3, 11, 2, 1, "f32")          # 11 * 40 bytes is not a multiple of 16
     batch = tg.tg_batch_create(3, 11, 16)
     tg.tg_batch_bin(batch, torch.rand((16, 3), device="cuda"))
-    with pytest.raises(tg.TGError):
-        tg.tg_query_binned(g, batch)
     with pytest.raises(tg.TGError):
         tg.tg_batch_create(2, 10, 16)
     with pytest.raises(tg.TGError):
