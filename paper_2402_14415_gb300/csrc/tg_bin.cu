@@ -20,7 +20,7 @@ namespace tg {
 constexpr int kBinThreads = 256;
 constexpr int kHistThreads = 1024;
 constexpr int kMaxSmemBins = 32768;   // 128 KB of shared counters
-constexpr int kCoarse = 64;           // bricks per coarse bin of the two-pass scatter
+constexpr int kCoarse = 64;           // most bricks per coarse bin of the two-pass scatter
 constexpr int kFineThreads = 512;
 
 __device__ __forceinline__ void load_point3(const float *__restrict__ pts, int64_t n, float *x)
@@ -176,7 +176,19 @@ bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int *
 // the tile is then written out in its sorted order, so that consecutive
 // threads store consecutive records of a run (coalesced lines instead of one
 // L2 request per 16-byte record).
-constexpr int kCoarseBins = kMaxSmemBins / kCoarse;          // 512
+constexpr int kCoarseBins = kHistThreads;                     // most coarse bins: one thread each in the scan
+static_assert(kCoarse % 32 == 0, "one warp lane per kCoarse / 32 bricks in the fine pass");
+
+// Bricks per coarse bin: the widest power of two up to kCoarse that still
+// gives the fine pass two blocks per SM, but no narrower than keeps the
+// coarse bins within one thread each of the coarse pass's block.
+static int coarse_width(int nbricks)
+{
+    int cw = kCoarse;
+    while (cw > 1 && (nbricks + cw - 1) / cw < 2 * num_sms()) cw >>= 1;
+    while ((nbricks + cw - 1) / cw > kCoarseBins) cw <<= 1;
+    return cw;
+}
 constexpr int kCoarseTile = 4 * kHistThreads;                // records per coarse tile
 constexpr int kFineTile = 4 * kFineThreads;                  // records per fine tile
 
@@ -204,60 +216,50 @@ struct FineSmem {
 // coarse bin is one contiguous run, filled tile by tile.
 __global__ void __launch_bounds__(kHistThreads)
 bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk, int res, int nbx, int nby,
-                        int nbricks, const int *__restrict__ hist, const int *__restrict__ offsets,
+                        int nbricks, int cw, const int *__restrict__ hist, const int *__restrict__ offsets,
                         float4 *__restrict__ coarse)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CoarseSmem &S = *reinterpret_cast<CoarseSmem *>(smem_raw);
-    const int ncoarse = (nbricks + kCoarse - 1) / kCoarse;
+    const int ncoarse = (nbricks + cw - 1) / cw;
     const int *h = hist + (int64_t)blockIdx.x * nbricks;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int cb = wid; cb < ncoarse; cb += blockDim.x >> 5) {     // one warp per coarse bin
         int sum = 0;
-        for (int j = lane; j < kCoarse; j += 32) {
-            const int b = cb * kCoarse + j;
+        for (int j = lane; j < cw; j += 32) {
+            const int b = cb * cw + j;
             if (b < nbricks) sum += __ldg(h + b);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) S.cur[cb] = __ldg(offsets + cb * kCoarse) + sum;
+        if (lane == 0) S.cur[cb] = __ldg(offsets + cb * cw) + sum;
     }
     const float scale = (float)(res - 1);
     const int64_t lo = (int64_t)blockIdx.x * chunk;
     const int64_t hi = min(N, lo + chunk);
     constexpr int U = kCoarseTile / kHistThreads;
-    // the next tile's points are loaded while this one is ranked, staged and written
-    float x[U][3], xn[U][3];
-    if (lo < hi) {
-        const int cnt0 = (int)min((int64_t)kCoarseTile, hi - lo);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = threadIdx.x + u * kHistThreads;
-            if (i < cnt0) load_point3(pts, lo + i, x[u]);
-        }
-    }
     for (int64_t t0 = lo; t0 < hi; t0 += kCoarseTile) {
         const int cnt = (int)min((int64_t)kCoarseTile, hi - t0);
-        const int cnt1 = (int)max((int64_t)0, min((int64_t)kCoarseTile, hi - (t0 + kCoarseTile)));
         for (int j = threadIdx.x; j < ncoarse; j += blockDim.x) S.cnt[j] = 0;
         __syncthreads();
+        float x[U][3];
         int key[U], rank[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = threadIdx.x + u * kHistThreads;
             key[u] = -1;
-            if (i < cnt) {
-                int c[3];
-                float t[3];
-                locate<3>(x[u], res, scale, c, t);
-                key[u] = brick_of(c, nbx, nby) / kCoarse;
-                rank[u] = atomicAdd(S.cnt + key[u], 1);
-            }
+            if (i < cnt) load_point3(pts, t0 + i, x[u]);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = threadIdx.x + u * kHistThreads;
-            if (i < cnt1) load_point3(pts, t0 + kCoarseTile + i, xn[u]);
+            if (i < cnt) {
+                int c[3];
+                float t[3];
+                locate<3>(x[u], res, scale, c, t);
+                key[u] = brick_of(c, nbx, nby) / cw;
+                rank[u] = atomicAdd(S.cnt + key[u], 1);
+            }
         }
         __syncthreads();
         {   // tile offsets per bin, and one run per bin reserved from the chunk's cursor
@@ -284,12 +286,6 @@ bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk,
             const int bkey = S.bin[q];
             coarse[S.gbase[bkey] + (q - S.loff[bkey])] = S.stage[q];
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            x[u][0] = xn[u][0];
-            x[u][1] = xn[u][1];
-            x[u][2] = xn[u][2];
-        }
         __syncthreads();
     }
 }
@@ -297,13 +293,13 @@ bin_coarse_place_kernel(const float *__restrict__ pts, int64_t N, int64_t chunk,
 // Fine place: one block per coarse bin scatters its records to their bricks,
 // tile by tile, and records the permutation.
 __global__ void __launch_bounds__(kFineThreads)
-bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int nby, int nbricks,
+bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int nby, int nbricks, int cw,
                       const int *__restrict__ offsets, float4 *__restrict__ sorted, int *__restrict__ perm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FineSmem &S = *reinterpret_cast<FineSmem *>(smem_raw);
-    const int b0 = blockIdx.x * kCoarse;
-    const int nb = min(kCoarse, nbricks - b0);
+    const int b0 = blockIdx.x * cw;
+    const int nb = min(cw, nbricks - b0);       // counters past nb stay zero
     for (int j = threadIdx.x; j < nb; j += blockDim.x) S.cur[j] = __ldg(offsets + b0 + j);
     const int lo = __ldg(offsets + b0), hi = __ldg(offsets + b0 + nb);
     const float scale = (float)(res - 1);
@@ -344,21 +340,29 @@ bin_fine_place_kernel(const float4 *__restrict__ coarse, int res, int nbx, int n
             if (i < cnt1) qn[u] = coarse[t0 + kFineTile + i];
         }
         __syncthreads();
-        if (threadIdx.x < 32) {   // one warp: offsets of the 64 bricks in the tile, and their runs
-            const int a = S.cnt[2 * lane], b = S.cnt[2 * lane + 1];
-            int incl = a + b;
+        if (threadIdx.x < 32) {   // one warp: offsets of the kCoarse bricks in the tile, and their runs
+            constexpr int PER = kCoarse / 32;
+            int a[PER], sum = 0;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                a[k] = S.cnt[PER * lane + k];
+                sum += a[k];
+            }
+            int incl = sum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int u = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += u;
             }
-            const int ex = incl - a - b;
-            S.loff[2 * lane] = ex;
-            S.loff[2 * lane + 1] = ex + a;
-            S.gbase[2 * lane] = S.cur[2 * lane];
-            S.gbase[2 * lane + 1] = S.cur[2 * lane + 1];
-            S.cur[2 * lane] += a;
-            S.cur[2 * lane + 1] += b;
+            int ex = incl - sum;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int j = PER * lane + k;
+                S.loff[j] = ex;
+                S.gbase[j] = S.cur[j];
+                S.cur[j] += a[k];
+                ex += a[k];
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -684,11 +688,12 @@ tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream strea
         if ((st = launch_status("tg_batch_bin: chunk scan")) != TG_OK) return st;
         bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, nullptr, nbr);
         if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;
+        const int cw = coarse_width(nbr);
         bin_coarse_place_kernel<<<b->G, kHistThreads, sizeof(CoarseSmem), s>>>(pts, N, chunk, b->res, nbx, nby, nbr,
-                                                                               b->hist, b->offsets, b->coarse);
+                                                                               cw, b->hist, b->offsets, b->coarse);
         if ((st = launch_status("tg_batch_bin: coarse place")) != TG_OK) return st;
-        bin_fine_place_kernel<<<(nbr + kCoarse - 1) / kCoarse, kFineThreads, sizeof(FineSmem), s>>>(
-            b->coarse, b->res, nbx, nby, nbr, b->offsets, b->sorted, b->perm);
+        bin_fine_place_kernel<<<(nbr + cw - 1) / cw, kFineThreads, sizeof(FineSmem), s>>>(
+            b->coarse, b->res, nbx, nby, nbr, cw, b->offsets, b->sorted, b->perm);
         return launch_status("tg_batch_bin: fine place");
     }
     if ((st = cuda_status(cudaMemsetAsync(b->counts, 0, (b->nbricks + 1) * sizeof(int), s), "tg_batch_bin")) != TG_OK)
