@@ -212,6 +212,72 @@ def run_cpu_baseline(path: str, steps: int, warmup: int):
                                 "coefficients of the GPU's grid, in a process of its own"}), flush=True)
 
 
+def run_oracle_timings():
+    """The FP64 oracle on the fits of the other configurations, timed on the host cores: the whole config-1 fit
+    (32^3 order 2, sphere, 2^16 points per step, L1, Adam lr 1e-2, 100 steps), and samples of the 256^3 fit
+    step (2^20 points, L1 + 0.1 eikonal, Adam) and of the ray-march training step (160^3 density order 2 +
+    colour order 1, 8192 rays x 256 samples, both Adam steps), extrapolated to 2000 and 3000 steps. Inputs are
+    generated before each timed region."""
+    import oracle
+    import workloads as W
+    out = {"cores": threads_used()}
+    # config 1, the whole fit
+    shape = W.sphere_shape()
+    res, order, n, steps = 32, 2, 1 << 16, 100
+    batches = [W.sdf_points(shape, seed=1, step=k, n=n) for k in range(steps)]
+    p = W.init_coefs(3, res, order, 1, seed=0, std=1e-3).astype(np.float64)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        g, _ = oracle.sdf_step(res, order, p, batches[k], shape.spheres, shape.boxes, 0.0)
+        oracle.adam(p, g, m, v, 1e-2, step=k + 1)
+    t1 = time.perf_counter()
+    ev = W.sdf_points(shape, seed=2, step=0, n=1 << 14)
+    f, _, _, _ = oracle.query(3, res, order, 1, p, ev, want_grad=False)
+    err = float(np.abs(f[:, 0] - oracle.sdf_union(shape.spheres, shape.boxes, ev.astype(np.float64))).mean())
+    out["config1_fit"] = {"s": t1 - t0, "steps": steps, "mean_abs_sdf_error": err, "kind": "measured"}
+    # config 2, a sample of the 256^3 fit step
+    shape = W.union_shape(0)
+    res, n, k_s = 256, 1 << 20, 2
+    batches = [W.sdf_points(shape, seed=1, step=k, n=n) for k in range(k_s)]
+    p = W.init_coefs(3, res, 2, 1, seed=0, std=1e-3).astype(np.float64)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    t0 = time.perf_counter()
+    for k in range(k_s):
+        g, _ = oracle.sdf_step(res, 2, p, batches[k], shape.spheres, shape.boxes, 0.1)
+        oracle.adam(p, g, m, v, 5e-3, step=k + 1)
+    per = (time.perf_counter() - t0) / k_s
+    out["config2_fit"] = {"s_per_step": per, "sampled_steps": k_s, "s_2000_steps_extrapolated": 2000 * per,
+                          "kind": "extrapolated from the sampled steps"}
+    del p, m, v, g
+    # config 4, a sample of the ray-march training step
+    res, R, S = 160, 8192, 256
+    dco = W.init_coefs(3, res, 2, 1, seed=0, std=0.5).astype(np.float64)
+    cco = W.init_coefs(3, res, 1, 3, seed=1, std=0.5).astype(np.float64)
+    r_s = 1024                                   # rays rendered per sample; the step's 8192 scale linearly
+    o, d = W.random_rays(7, R, radius=1.5, spread=0.35)
+    tgt = np.random.default_rng(0).random((R, 3)).astype(np.float32)
+    md, vd, mc, vc = (np.zeros_like(a) for a in (dco, dco, cco, cco))
+    t0 = time.perf_counter()
+    _, _, dg, cg = oracle.render(res, 2, dco, 1, cco, o[:r_s], d[:r_s], S, seed=0, target=tgt[:r_s])
+    t1 = time.perf_counter()
+    oracle.adam(dco, dg, md, vd, 0.1, step=1)
+    oracle.adam(cco, cg, mc, vc, 0.03, step=1)
+    t2 = time.perf_counter()
+    per = (t1 - t0) * R / r_s + (t2 - t1)
+    out["config4_render_fit"] = {"s_per_step": per, "sampled": f"{r_s} of the step's {R} rays (scaled by {R // r_s}) "
+                                 "and both Adam steps in full", "s_3000_steps_extrapolated": 3000 * per,
+                                 "kind": "extrapolated from the sampled step"}
+    print(json.dumps(out), flush=True)
+
+
+def oracle_timings_of():
+    """run_oracle_timings in a process of its own (no CUDA context beside the oracle's threads)."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-timings"], capture_output=True,
+                       text=True, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -391,6 +457,8 @@ def run_ours(args, world, rank, local):
             line["configs"]["serving_burst"] = bench_burst()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_of(tg.tg_get_coefs(g).cpu().numpy())      # the very grid the GPU ran on
+        if not args.no_extras:
+            line["oracle_timings"] = oracle_timings_of()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -996,9 +1064,12 @@ def main():
     ap.add_argument("--profile-serve", action="store_true",
                     help="run six fit jobs of one group through the server for three steps (for ncu captures)")
     ap.add_argument("--cpu-baseline-from", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-timings", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_baseline_from:
         return run_cpu_baseline(args.cpu_baseline_from, args.steps, args.warmup)
+    if args.oracle_timings:
+        return run_oracle_timings()
     args.warmup = max(args.warmup, 3)
     if args.profile:
         return profile_once()

@@ -41,7 +41,7 @@ tg_status dev_alloc(void **p, size_t bytes, const char *what);
 tg_status dev_alloc_async(void **p, size_t bytes, cudaStream_t s, const char *what);
 
 int num_sms();                      // SM count of the current device (cached per device)
-constexpr int kBinChunksPerSm = 1;  // point chunks of the binning per SM (one histogram row each; 2 measured slower)
+constexpr int kBinChunksPerSm = 2;  // point chunks of the binning per SM (one histogram row each): two coarse-pass blocks share an SM
 // Resident blocks per SM of a kernel at a launch shape (cached per device and kernel).
 int blocks_per_sm(const void *kernel, int threads, size_t smem);
 
