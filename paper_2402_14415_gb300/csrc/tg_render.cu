@@ -97,8 +97,11 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-template <typename TD, typename TC, int OD, int OC>
-__global__ void __launch_bounds__(256)
+// MPL: the most samples a lane holds (8 for S <= 256, 16 for S <= 512); the
+// per-sample state lives in registers, so a smaller MPL leaves room for two
+// blocks per SM.
+template <typename TD, typename TC, int OD, int OC, int MPL>
+__global__ void __launch_bounds__(256, MPL <= 8 ? 2 : 1)
 render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int res, const float *__restrict__ ro,
               const float *__restrict__ rd, int64_t R, int S, uint64_t seed, uint64_t ray_base, float bg,
               float *__restrict__ rgb, const float *__restrict__ target, const float *__restrict__ dldc, float inv_r,
@@ -115,18 +118,17 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
         const uint64_t key = stream_key(seed, ray_base + (uint64_t)r);
         // sample positions by the FP32 rule t_i = tn + (i + xi_i) step, every operation rounded once
         const float step = hit ? __fdiv_rn(__fsub_rn(tf, tn), (float)S) : 0.f;
-        // per-lane samples: optical depth tau = sigma delta, colour, raw field values
-        float tau[kMaxSamplesPerLane], col[kMaxSamplesPerLane][3], fd[kMaxSamplesPerLane], dlt[kMaxSamplesPerLane];
-        float xsmp[kMaxSamplesPerLane][3];
+        // per-lane samples: optical depth tau = sigma delta, colour, raw field values (positions are
+        // recomputed by the same FP32 operations where the backward needs them)
+        float tau[MPL], col[MPL][3], fd[MPL], dlt[MPL];
         float lane_tau = 0.f;
 #pragma unroll
-        for (int k = 0; k < kMaxSamplesPerLane; ++k) {
+        for (int k = 0; k < MPL; ++k) {
             const int i = lane * m + k;
             tau[k] = 0.f;
             fd[k] = 0.f;
             dlt[k] = 0.f;
             col[k][0] = col[k][1] = col[k][2] = 0.f;
-            xsmp[k][0] = xsmp[k][1] = xsmp[k][2] = 0.f;
             if (k < m && i < S && hit) {
                 const float ti = __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, uniform_k(key, (uint64_t)i)), step));
                 const float tnext =
@@ -139,10 +141,7 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
                 dlt[k] = tnext - ti;
                 tau[k] = softplus_f(fd[k]) * dlt[k];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    col[k][a] = sigmoid_f(fc[a]);
-                    xsmp[k][a] = x[a];
-                }
+                for (int a = 0; a < 3; ++a) col[k][a] = sigmoid_f(fc[a]);
                 lane_tau += tau[k];
             }
         }
@@ -150,9 +149,9 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
         const float before = warp_excl_scan(lane_tau, total_tau);
         // Eq. 10: T_i = exp(-sum_{j<i} tau_j), weight T_i (1 - exp(-tau_i))
         float acc[3] = {0.f, 0.f, 0.f}, run = before;
-        float Ti[kMaxSamplesPerLane];
+        float Ti[MPL];
 #pragma unroll
-        for (int k = 0; k < kMaxSamplesPerLane; ++k) {
+        for (int k = 0; k < MPL; ++k) {
             Ti[k] = expf(-run);
             const float wgt = Ti[k] * -expm1f(-tau[k]);       // T_i alpha_i, alpha_i without the 1 - exp cancellation
 #pragma unroll
@@ -186,7 +185,7 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
 #pragma unroll
         for (int a = 0; a < 3; ++a) behind[a] = warp_excl_suffix(acc[a]) + T_end * bg;
 #pragma unroll
-        for (int k = kMaxSamplesPerLane - 1; k >= 0; --k) {
+        for (int k = MPL - 1; k >= 0; --k) {
             const int i = lane * m + k;
             if (!(k < m && i < S)) continue;
             const float alpha = -expm1f(-tau[k]);
@@ -202,7 +201,10 @@ render_kernel(const TD *__restrict__ dcoef, const TC *__restrict__ ccoef, int re
             }
             const int64_t sidx = r * S + i;
             if (hit) {
-                xs[3 * sidx] = xsmp[k][0]; xs[3 * sidx + 1] = xsmp[k][1]; xs[3 * sidx + 2] = xsmp[k][2];
+                const float ti = __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, uniform_k(key, (uint64_t)i)), step));
+                xs[3 * sidx] = fmaf(ti, d[0], o[0]);
+                xs[3 * sidx + 1] = fmaf(ti, d[1], o[1]);
+                xs[3 * sidx + 2] = fmaf(ti, d[2], o[2]);
             } else {
                 // a missed ray's samples carry zero upstream gradient; spread them over the cube (a
                 // low-discrepancy sequence of the sample index) so the binned backward's bricks stay
@@ -252,10 +254,12 @@ static tg_status render_impl(const tg_grid *dg, const tg_grid *cg, const float *
     int64_t cap = (int64_t)num_sms() * 8;
     unsigned nb = (unsigned)(need < cap ? need : cap);
     const float inv_r = 1.0f / (float)R;
-#define TG_RK(TD, TC, OD, OC)                                                                              \
-    render_kernel<TD, TC, OD, OC><<<nb, 256, 0, s>>>((const TD *)dg->store, (const TC *)cg->store, dg->res, \
-                                                     rays_o, rays_d, R, S, seed, ray_base, bg, rgb_out,       \
-                                                     target_rgb, dldc, inv_r, loss_sum, xs, ud, uc)
+#define TG_RK2(TD, TC, OD, OC, MPL)                                                                             \
+    render_kernel<TD, TC, OD, OC, MPL><<<nb, 256, 0, s>>>((const TD *)dg->store, (const TC *)cg->store, dg->res, \
+                                                          rays_o, rays_d, R, S, seed, ray_base, bg, rgb_out,       \
+                                                          target_rgb, dldc, inv_r, loss_sum, xs, ud, uc)
+#define TG_RK(TD, TC, OD, OC) \
+    do { if (S <= 256) TG_RK2(TD, TC, OD, OC, 8); else TG_RK2(TD, TC, OD, OC, 16); } while (0)
     const int key = dg->order * 10 + cg->order;
     if (dg->dtype == TG_F32 && cg->dtype == TG_F32) {
         if (key == 21) TG_RK(float, float, 2, 1); else if (key == 0) TG_RK(float, float, 0, 0);
@@ -269,6 +273,7 @@ static tg_status render_impl(const tg_grid *dg, const tg_grid *cg, const float *
         return fail(TG_EINVAL, "%s: both grids must be FP32 or both BF16", who);
     }
 #undef TG_RK
+#undef TG_RK2
     if ((st = launch_status(who)) != TG_OK || !train) return st;
     // coefficient gradients of both grids through the binned backward
     if ((st = tg_batch_bin(batch, xs, NS, s)) != TG_OK) return st;
