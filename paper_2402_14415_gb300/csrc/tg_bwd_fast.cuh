@@ -18,7 +18,8 @@
 //      local coordinate l of the point and the vertex coordinate v,
 //      d = l - v = t - b exactly (both lie on the FP32 grid of u), so
 //      A = 1 - |d| (= 1 - t or t, exact where t - b is) and U = d h need no
-//      corner bits,
+//      corner bits; the sums are taken in d and scaled by h, h^2 / 2 or h^2
+//      once per vertex,
 //   5. stores the sums as the 9^3 tile for one TMA bulk-tensor reduce-add into
 //      the gradient.
 #pragma once
@@ -219,39 +220,42 @@ brick_bwd_fast_kernel(const __grid_constant__ CUtensorMap gmap, int res, int nbx
                 const float4 q = *reinterpret_cast<const float4 *>(qp);
                 const float dx = q.x - fvx, dy = q.y - fvy, dz = q.z - fvz;      // t - b per axis
                 const float w = (1.f - fabsf(dx)) * (1.f - fabsf(dy)) * (1.f - fabsf(dz));
-                float ux = 0.f, uy = 0.f, uz = 0.f;
-                if constexpr (ORDER >= 1) {
-                    ux = dx * h;                                    // (t - b) h
-                    uy = dy * h;
-                    uz = dz * h;
-                }
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
                     const float S = w * (C == 1 ? q.w : qp[4 + ch]);
                     float *ac = acc + ch * K;
                     ac[0] += S;
-                    if constexpr (ORDER >= 1) {
-                        const float sux = S * ux, suy = S * uy, suz = S * uz;
-                        ac[1] += sux;
-                        ac[2] += suy;
-                        ac[3] += suz;
+                    if constexpr (ORDER >= 1) {   // in grid units t - b; the powers of h are applied per vertex
+                        const float sdx = S * dx, sdy = S * dy, sdz = S * dz;
+                        ac[1] += sdx;
+                        ac[2] += sdy;
+                        ac[3] += sdz;
                         if constexpr (ORDER >= 2) {
-                            ac[4] = fmaf(sux, ux, ac[4]);          // twice the delta^2 / 2 terms
-                            ac[5] = fmaf(suy, uy, ac[5]);
-                            ac[6] = fmaf(suz, uz, ac[6]);
-                            ac[7] = fmaf(sux, uy, ac[7]);
-                            ac[8] = fmaf(sux, uz, ac[8]);
-                            ac[9] = fmaf(suy, uz, ac[9]);
+                            ac[4] = fmaf(sdx, dx, ac[4]);          // twice the delta^2 / 2 terms
+                            ac[5] = fmaf(sdy, dy, ac[5]);
+                            ac[6] = fmaf(sdz, dz, ac[6]);
+                            ac[7] = fmaf(sdx, dy, ac[7]);
+                            ac[8] = fmaf(sdx, dz, ac[8]);
+                            ac[9] = fmaf(sdy, dz, ac[9]);
                         }
                     }
                 }
             }
-            if constexpr (ORDER >= 2) {
+            if constexpr (ORDER >= 1) {       // delta = (t - b) h: first-order sums take h, second-order h^2
+                const float h2 = h * h, hh2 = 0.5f * h * h;
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
-                    acc[ch * K + 4] *= 0.5f;
-                    acc[ch * K + 5] *= 0.5f;
-                    acc[ch * K + 6] *= 0.5f;
+                    acc[ch * K + 1] *= h;
+                    acc[ch * K + 2] *= h;
+                    acc[ch * K + 3] *= h;
+                    if constexpr (ORDER >= 2) {
+                        acc[ch * K + 4] *= hh2;
+                        acc[ch * K + 5] *= hh2;
+                        acc[ch * K + 6] *= hh2;
+                        acc[ch * K + 7] *= h2;
+                        acc[ch * K + 8] *= h2;
+                        acc[ch * K + 9] *= h2;
+                    }
                 }
             }
             float *dst = tile + (v / kBV) * BXI + (v % kBV) * NV;
