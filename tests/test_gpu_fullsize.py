@@ -92,3 +92,35 @@ def test_spatial_gradient_and_bf16_storage_at_full_size(tg, inputs):
         stored = tg.tg_get_coefs(g, which=0).cpu().numpy().astype(np.float64)    # dequantised for BF16
         check_forward(out.cpu().numpy()[sample], gx.cpu().numpy()[sample], 3, RES, ORDER, 1, stored, pts[sample])
         del g
+
+
+def test_fit_sized_batch_on_the_record_path(tg):
+    """The SDF fit's batch on the full grid: 2^20 points (half uniform, half on the union's surface), 32 points
+    per brick, so the binned forward with spatial gradients and the backward with value and spatial-gradient
+    upstreams take one thread per record. Sampled outputs and a z-slab of the gradient against the oracle."""
+    shape = W.union_shape(0)
+    n = 1 << 20
+    pts = W.sdf_points(shape, seed=1, step=0, n=n)
+    r = np.random.default_rng(6)
+    up = r.normal(size=(n, 1)).astype(np.float32)
+    ug = r.normal(size=(n, 1, 3)).astype(np.float32)
+    g = tg.tg_create(3, RES, ORDER, 1, "f32", seed=0, init_std=1.0)
+    batch = tg.tg_batch_create(3, RES, n)
+    tg.tg_batch_bin(batch, to_dev(pts))
+    out, gx = tg.tg_query_binned(g, batch, want_grad=True)
+    grad = torch.zeros(g.n_coefs, device="cuda")
+    tg.tg_query_backward_binned(g, batch, to_dev(up), grad, dL_dgradx=to_dev(ug))
+    torch.cuda.synchronize()
+    coefs = tg.tg_get_coefs(g, which=0).cpu().numpy().astype(np.float64)
+    sample = np.random.default_rng(2).choice(n, 1 << 16, replace=False)
+    check_forward(out.cpu().numpy()[sample], gx.cpu().numpy()[sample], 3, RES, ORDER, 1, coefs, pts[sample])
+    cz = cells_z(pts)
+    z0, z1 = 120, 136
+    sel = (cz >= z0) & (cz < z1)
+    ref, A = oracle.query_backward(3, RES, ORDER, 1, pts[sel], up[sel].astype(np.float64),
+                                   ug[sel].astype(np.float64), want_abs=True)
+    lo, hi = (z0 + 1) * RES * RES * K, z1 * RES * RES * K
+    err = np.abs(grad.cpu().numpy()[lo:hi].astype(np.float64) - ref[lo:hi])
+    tol = GRAD_RTOL * np.maximum(np.abs(ref[lo:hi]), A[lo:hi]) + 1e-30
+    assert (err <= tol).all(), f"{(err > tol).sum()} gradient entries off"
+    assert (A[lo:hi] > 0).mean() > 0.1           # a few hundred thousand slab entries were reached
