@@ -441,6 +441,7 @@ def run_ours(args, world, rank, local):
                      "model": "compulsory bytes: 16 B/point + K*4 B (fwd) or 2*K*4 B (bwd) per touched vertex"},
         "step_roofline": {"bytes": fwd_bytes + bwd_bytes, "achieved_gbs": (fwd_bytes + bwd_bytes) / (ms * 1e-3) / 1e9,
                           "frac": (fwd_bytes + bwd_bytes) / (ms * 1e-3) / 1e9 / hbm},
+        "alu_roofline": alu_roofline(tg, N, kernels["forward"]),
         "clocks": clocks,
         "e2e": {"value": world * N / (ms_e2e * 1e-3) / 1e6, "unit": "Mpts/s",
                 "h2d_bytes_per_step": int(pts_np.nbytes + up_np.nbytes), "d2h_bytes_per_step": int(N * 4),
@@ -461,6 +462,20 @@ def run_ours(args, world, rank, local):
             line["oracle_timings"] = oracle_timings_of()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def alu_roofline(tg, n_points: int, fwd_ms: float):
+    """The forward against the measured FP32 FMA peak (tg_measure_fp32_peak), on an operation-count model of
+    Eq. 2 - Eq. 4 at order 2, one channel: per corner the 10-term series as 10 multiply-adds (20 FLOP) on the
+    offset products (3 offsets and 6 products, 9 FLOP) and the blend (2 FLOP); per point the 8 corner weights
+    (12 multiplies) and the index rule (6). 8 x 31 + 18 = 266 FLOP per point."""
+    flop_per_point = 8 * 31 + 18
+    peak = tg.tg_measure_fp32_peak()
+    achieved = n_points * flop_per_point / (fwd_ms * 1e-3) / 1e12
+    return {"kernel": "brick_fwd_kernel (tg_query_binned)", "flop_per_point": flop_per_point,
+            "model": "operation count of Eq. 2 - Eq. 4 at order 2",
+            "achieved_tflops": achieved, "peak_tflops": peak, "peak_kind": "measured (tg_measure_fp32_peak)",
+            "frac": achieved / peak}
 
 
 def _time_ms(fn, steps, warmup):

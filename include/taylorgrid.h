@@ -83,6 +83,14 @@ TG_API const char *tg_last_error(void);
  * TG_ENOMEM and frees what it had allocated. Errors: TG_EINVAL (negative). */
 TG_API tg_status tg_inject_alloc_failures(int pass, int fail);
 
+/* Measured FP32 FMA throughput of the current device (no paper counterpart):
+ * the denominator of the ALU roofline beside the measured HBM copy peak. A
+ * kernel of independent fused multiply-add chains, one resident wave of blocks
+ * per SM, is timed with CUDA events after one warm-up launch; *tflops receives
+ * 2 x FMAs / seconds / 1e12. Synchronous: it waits for the device, allocates
+ * and frees 4 bytes. Errors: TG_EINVAL (NULL), TG_ENOMEM, TG_EDEVICE. */
+TG_API tg_status tg_measure_fp32_peak(double *tflops);
+
 /* ---------------------------------------------------------------------------
  * Grid storage V_T (Sec. 3.1: "a dense grid G of size w x d x h", each vertex
  * storing the low-order Taylor series).

@@ -87,6 +87,7 @@ _SIGS = {
     "tg_batch_timeouts": [_vp, ctypes.POINTER(_int)],
     "tg_grid_timeouts": [_vp, ctypes.POINTER(_int)],
     "tg_inject_alloc_failures": [_int, _int],
+    "tg_measure_fp32_peak": [ctypes.POINTER(ctypes.c_double)],
     "tg_noalloc_timeouts": [ctypes.POINTER(_int)],
     "tg_batch_gather": [_vp, _vp, _int, _vp, _vp],
     "tg_batch_scatter": [_vp, _vp, _int, _vp, _vp],
@@ -356,6 +357,13 @@ def tg_batch_scatter(batch: Batch, src: torch.Tensor, dst=None, stream=None) -> 
 def tg_batch_timeouts(batch: Batch) -> int:
     v = _int(0)
     _check(load().tg_batch_timeouts(batch.handle, ctypes.byref(v)), "tg_batch_timeouts")
+    return v.value
+
+
+def tg_measure_fp32_peak() -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s (the ALU roofline's denominator)."""
+    v = ctypes.c_double()
+    _check(load().tg_measure_fp32_peak(ctypes.byref(v)), "tg_measure_fp32_peak")
     return v.value
 
 
