@@ -11,6 +11,7 @@
 // input index) for tg_batch_order and the row permutations.
 #include <stdlib.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "tg_binned.cuh"
@@ -689,17 +690,20 @@ tg_status tg_batch_bin(tg_batch *b, const float *pts, int64_t N, tg_stream strea
     tg_status st;
     if (N == 0) return cuda_status(cudaMemsetAsync(b->offsets, 0, (b->nbricks + 1) * sizeof(int), s), "tg_batch_bin");
     if (b->G) {
-        const int64_t chunk = (N + b->G - 1) / b->G;
+        // two point chunks per SM pay for their histogram rows (G x bricks ints, written and read back) only
+        // on large batches: below 2^22 points one chunk per SM is faster
+        const int G = N >= ((int64_t)1 << 22) ? b->G : std::max(1, b->G / kBinChunksPerSm);
+        const int64_t chunk = (N + G - 1) / G;
         const int smem = nbr * (int)sizeof(int);
-        bin_hist_kernel<<<b->G, kHistThreads, smem, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist);
+        bin_hist_kernel<<<G, kHistThreads, smem, s>>>(pts, N, chunk, b->res, nbx, nby, nbr, b->hist);
         if ((st = launch_status("tg_batch_bin: histogram")) != TG_OK) return st;
-        bin_chunk_scan_kernel<<<(nbr + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(b->hist, b->G, nbr,
+        bin_chunk_scan_kernel<<<(nbr + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(b->hist, G, nbr,
                                                                                             b->counts);
         if ((st = launch_status("tg_batch_bin: chunk scan")) != TG_OK) return st;
         bin_scan_kernel<<<1, 1024, 0, s>>>(b->counts, b->offsets, nullptr, nbr);
         if ((st = launch_status("tg_batch_bin: scan")) != TG_OK) return st;
         const int cw = coarse_width(nbr);
-        bin_coarse_place_kernel<<<b->G, kCoarseThreads, sizeof(CoarseSmem), s>>>(pts, N, chunk, b->res, nbx, nby, nbr,
+        bin_coarse_place_kernel<<<G, kCoarseThreads, sizeof(CoarseSmem), s>>>(pts, N, chunk, b->res, nbx, nby, nbr,
                                                                                cw, b->hist, b->offsets, b->coarse);
         if ((st = launch_status("tg_batch_bin: coarse place")) != TG_OK) return st;
         bin_fine_place_kernel<<<(nbr + cw - 1) / cw, kFineThreads, sizeof(FineSmem), s>>>(
