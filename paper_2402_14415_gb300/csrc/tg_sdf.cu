@@ -2,6 +2,7 @@
 // batches, the per-point loss (Eq. 6 with w = 1, eikonal term of Eq. 8) and
 // the fitting step that composes binning, the binned forward with spatial
 // gradients, the loss and the binned backward - all in binned order.
+#include "tg_records.cuh"
 #include "tg_sdf.cuh"
 
 namespace tg {
@@ -133,6 +134,45 @@ sdf_error_kernel(ShapeView s, const T *__restrict__ coefs, int res, const float 
     }
 }
 
+// The SDF step on the record path in one pass: for every binned record, f and
+// grad f (Eq. 2 - Eq. 4), the target distance, the upstreams of the L1 /
+// Eq. 7 term and of the eikonal term (sdf_point_upstream), and the coefficient
+// gradient added with the warp-aggregated vector reductions of the records
+// backward; the loss sums as sdf_loss_kernel forms them. Nothing per point
+// goes through memory between the stages.
+template <typename T, int ORDER, bool EIK>
+__global__ void __launch_bounds__(256)
+sdf_records_step_kernel(ShapeView s, const T *__restrict__ coefs, int res, const float4 *__restrict__ sorted,
+                        int64_t N, float lambda, float k_weight, float inv_n, float *__restrict__ grad,
+                        float *__restrict__ sums)
+{
+    __shared__ float tmp[32];
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float l1 = 0.f, eik = 0.f;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < N; base += stride) {
+        const int64_t p = base + lane;
+        const unsigned valid = __ballot_sync(0xffffffffu, p < N);
+        if (p >= N) break;
+        const float4 q = sorted[p];
+        const float x[3] = {q.x, q.y, q.z};
+        float f[1], gu[1][3];
+        point_eval<T, 3, ORDER, 1>(coefs, res, x, f, gu);
+        const float d = sdf_union(s, clamp01(q.x), clamp01(q.y), clamp01(q.z));
+        float uf[1], ug[1][3], a, e;
+        sdf_point_upstream(f[0], EIK ? gu[0] : nullptr, d, lambda, k_weight, inv_n, uf, ug[0], &a, &e);
+        l1 += a;
+        eik += e;
+        point_scatter<3, ORDER, 1>(res, x, uf, ug, EIK, lane, valid, grad);
+    }
+    const float a = block_sum(l1, tmp);
+    if (threadIdx.x == 0) atomicAdd(sums, a);
+    if (EIK) {
+        const float b = block_sum(eik, tmp);
+        if (threadIdx.x == 0) atomicAdd(sums + 1, b);
+    }
+}
+
 static unsigned blocks_for(int64_t n, int per_sm = 8)
 {
     int64_t need = (n + 255) / 256, cap = (int64_t)num_sms() * per_sm;
@@ -154,6 +194,27 @@ tg_status sdf_step_impl(const tg_grid *g, tg_batch *bt, const ShapeView &s, cons
         pts = sampled;
     }
     if ((st = tg_batch_bin(bt, pts, N, cs)) != TG_OK) return st;
+    if (!deterministic && g->C == 1 && use_records_path(N, bt->nbricks, eik, true)) {
+        // few points per brick: forward, loss and backward in one pass over the records
+        const unsigned nb = records_blocks(N);
+        const float inv_n = 1.0f / (float)N;
+#define TG_RS(T, O)                                                                                               \
+    (eik ? (sdf_records_step_kernel<T, O, true><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, bt->sorted, N,  \
+                                                                     lambda_eik, k_weight, inv_n, coef_grad,        \
+                                                                     loss_sums), 0)                                 \
+         : (sdf_records_step_kernel<T, O, false><<<nb, 256, 0, cs>>>(s, (const T *)g->store, g->res, bt->sorted, N, \
+                                                                      lambda_eik, k_weight, inv_n, coef_grad,       \
+                                                                      loss_sums), 0))
+        if (g->dtype == TG_F32) {
+            if (g->order == 0) TG_RS(float, 0); else if (g->order == 1) TG_RS(float, 1); else TG_RS(float, 2);
+        } else if (g->dtype == TG_BF16) {
+            if (g->order == 0) TG_RS(__nv_bfloat16, 0); else if (g->order == 1) TG_RS(__nv_bfloat16, 1); else TG_RS(__nv_bfloat16, 2);
+        } else {
+            if (g->order == 0) TG_RS(__half, 0); else if (g->order == 1) TG_RS(__half, 1); else TG_RS(__half, 2);
+        }
+#undef TG_RS
+        return launch_status("tg_sdf_step: records step");
+    }
     if ((st = tg_query_binned(g, bt, f, eik ? gx : nullptr, TG_ORDER_BINNED, cs)) != TG_OK) return st;
     sdf_loss_kernel<<<blocks_for(N), 256, 0, cs>>>(s, bt->sorted, N, f, eik ? gx : nullptr, lambda_eik, k_weight,
                                                    1.0f / (float)N, uf, ug, loss_sums);
