@@ -35,15 +35,26 @@ constexpr int kBrick = 8;                              // cells per brick edge
 constexpr int kBV = kBrick + 1;                        // vertices per brick edge
 constexpr int kBrickCells = kBrick * kBrick * kBrick;  // 512
 
-// Elements per brick row in a TMA box: the 9 vertex blocks padded to 16 bytes.
+// Bytes of one brick row in a TMA box: the 9 vertex blocks padded to 16 bytes.
+// 16-bit order-2 blocks (20 bytes) take a 208-byte row instead of 192: a
+// 52-word row pitch shifts consecutive rows by 20 banks, against 16 for 48
+// words (every second row on the same banks), which with cells sorted y
+// fastest spreads the forward's tile reads over more banks; the box reads 16
+// bytes of the next vertices it does not use.
+constexpr int box_row_bytes(int nv, int elem)
+{
+    return (elem == 2 && nv == 10) ? 208 : (kBV * nv * elem + 15) / 16 * 16;
+}
+
+// Elements per brick row in a TMA box.
 template <typename T, int NV>
 struct BoxInner {
-    static constexpr int bytes = (kBV * NV * (int)sizeof(T) + 15) / 16 * 16;
+    static constexpr int bytes = box_row_bytes(NV, (int)sizeof(T));
     static constexpr int value = bytes / (int)sizeof(T);
     static constexpr int tile_bytes = kBV * kBV * bytes;   // a full 9 x 9 x 9 brick
 };
 
-inline int box_inner_host(int nv, int elem) { return ((kBV * nv * elem + 15) / 16 * 16) / elem; }
+inline int box_inner_host(int nv, int elem) { return box_row_bytes(nv, elem) / elem; }
 
 __device__ __forceinline__ int brick_of(const int *c, int nbx, int nby)
 {
