@@ -34,8 +34,12 @@ def test_device_sampler_matches_generator(tg, shape_fn):
     assert close.mean() > 0.999
 
 
+@pytest.mark.parametrize("path", ["brick", "records"])
 @pytest.mark.parametrize("lam,k", [(0.0, 0.0), (0.1, 0.0), (0.1, 50.0)])
-def test_sdf_step_matches_oracle(tg, lam, k):
+def test_sdf_step_matches_oracle(tg, lam, k, path, monkeypatch):
+    """Both forms of the step: the binned forward, loss kernel and brick backward, and (forced here; chosen by
+    itself below 48 or 96 points per brick) the single kernel over the binned records."""
+    monkeypatch.setenv("TG_BINNED_PATH", path)
     res, order = 34, 2
     shape = W.union_shape(0)
     coefs = W.init_coefs(3, res, order, 1, seed=4, std=0.05)
@@ -64,9 +68,13 @@ def test_sdf_step_matches_oracle(tg, lam, k):
     assert (err <= GRAD_RTOL * np.maximum(np.abs(ref), A) + 1e-12).all(), err.max()
 
 
-def test_fit_sphere_32_order2_matches_oracle_fit(tg):
+@pytest.mark.parametrize("path", ["auto", "records"])
+def test_fit_sphere_32_order2_matches_oracle_fit(tg, path, monkeypatch):
     """Config-1 shape at reduced steps: both sides see the same batches; the final
-    error against the analytic SDF agrees (trajectory parity is unpinned)."""
+    error against the analytic SDF agrees (trajectory parity is unpinned). Again with
+    the step forced onto the single kernel over the binned records."""
+    if path != "auto":
+        monkeypatch.setenv("TG_BINNED_PATH", path)
     res, order, n, steps, lr = 32, 2, 1 << 14, 30, 1e-2
     shape = W.sphere_shape()
     coefs = W.init_coefs(3, res, order, 1, seed=0, std=1e-3)
