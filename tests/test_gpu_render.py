@@ -30,7 +30,7 @@ def grids(tg, res, dtype="f32", seed=3):
     return dg, cg, dco, cco
 
 
-@pytest.mark.parametrize("S", [32, 100, 256])
+@pytest.mark.parametrize("S", [32, 100, 256, 384, 512])      # up to 8 and up to 16 samples a lane
 def test_render_forward_matches_oracle(tg, S):
     res = 10
     dg, cg, dco, cco = grids(tg, res)
@@ -61,7 +61,7 @@ def test_render_homogeneous_closed_form(tg):
         np.testing.assert_allclose(rgb[r], c * (1 - T) + T, atol=2e-5)
 
 
-@pytest.mark.parametrize("dtype,S", [("f32", 48), ("bf16", 48), ("f32", 256), ("bf16", 256)])
+@pytest.mark.parametrize("dtype,S", [("f32", 48), ("bf16", 48), ("f32", 256), ("bf16", 256), ("f32", 400)])
 def test_render_training_gradients_match_oracle(tg, dtype, S):
     """Both coefficient gradients against the oracle's (Eq. 10 - Eq. 11 differentiated) at the scale-aware
     1e-4: |gpu - oracle| <= 1e-4 max(|oracle|, A), A the magnitude of the terms of that gradient. S = 256 is the
