@@ -23,16 +23,48 @@ __global__ void sdf_target_kernel(ShapeView s, const float *__restrict__ pts, in
         d[n] = sdf_union(s, clamp01(pts[3 * n]), clamp01(pts[3 * n + 1]), clamp01(pts[3 * n + 2]));
 }
 
+// The fit batch of `step`, the same points as sample_sdf_point. The uniform
+// half is one pass. For the surface half every lane runs a queue of its points
+// with one candidate draw per iteration and moves to its next point as soon as
+// the current one is accepted (or has used its 8 draws), so a lane whose point
+// was accepted at once does not wait for the warp's slowest point.
 __global__ void sdf_sample_kernel(ShapeView s, uint64_t seed, int64_t step, const int64_t *__restrict__ step_dev,
                                   int64_t N, float jitter, float *__restrict__ pts)
 {
+    constexpr uint64_t SLOTS = 16;
     if (step_dev) step = *step_dev;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        float p[3];
-        sample_sdf_point(s, seed, step, N, j, jitter, p);
-        pts[3 * j] = p[0];
-        pts[3 * j + 1] = p[1];
-        pts[3 * j + 2] = p[2];
+    const int64_t n_uni = N / 2;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t base = (uint64_t)step * 256ull;
+    const uint64_t key_u = stream_key(seed, base + 255ull);
+    for (int64_t j = tid; j < n_uni; j += stride) {
+        const uint64_t b = (uint64_t)j * SLOTS;
+        pts[3 * j] = clamp01(uniform_k(key_u, b));
+        pts[3 * j + 1] = clamp01(uniform_k(key_u, b + 1));
+        pts[3 * j + 2] = clamp01(uniform_k(key_u, b + 2));
+    }
+    int64_t j = n_uni + tid;
+    int a = 0;
+    while (j < N) {
+        const uint64_t b = (uint64_t)j * SLOTS;
+        const uint64_t key = stream_key(seed, base + (uint64_t)a);
+        float cand[3];
+        surface_candidate(s, uniform_k(key, b), uniform_k(key, b + 1), uniform_k(key, b + 8), uniform_k(key, b + 9),
+                          cand);
+        const bool accepted = sdf_union(s, cand[0], cand[1], cand[2]) > -1e-6f;
+        if (accepted || a == 7) {
+            float p[3];
+            if (accepted) {
+                p[0] = cand[0]; p[1] = cand[1]; p[2] = cand[2];
+            } else {
+                p[0] = uniform_k(key_u, b); p[1] = uniform_k(key_u, b + 1); p[2] = uniform_k(key_u, b + 2);
+            }
+            finish_surface_point(key_u, j, jitter, p, pts + 3 * j);
+            j += stride;
+            a = 0;
+        } else {
+            ++a;
+        }
     }
 }
 

@@ -112,6 +112,21 @@ __device__ __forceinline__ void sample_sdf_point(const ShapeView &s, uint64_t se
     out[2] = clamp01(p[2]);
 }
 
+// The final position of surface point j: p (the accepted candidate, or the
+// uniform fallback after 8 rejected ones) plus its jitter, clamped; the same
+// operations as the end of sample_sdf_point.
+__device__ __forceinline__ void finish_surface_point(uint64_t key_u, int64_t j, float jitter, float *p, float *out)
+{
+    constexpr uint64_t SLOTS = 16;
+    if (jitter > 0.f) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p[k] += jitter * normal_k(key_u, (uint64_t)j * (SLOTS / 2) + 2 + k);
+    }
+    out[0] = clamp01(p[0]);
+    out[1] = clamp01(p[1]);
+    out[2] = clamp01(p[2]);
+}
+
 // Upstream gradients of one point's loss terms (Eq. 6 with Eq. 7's weight,
 // and the eikonal term of Eq. 8): r = f - d, dL/df = w sign(r) / N, and
 // dL/d(grad_x f) = lambda 2 (|g| - 1) g / |g| / N (0 below |g| = 1e-12).
