@@ -249,6 +249,14 @@ TG_API tg_status tg_batch_bin(tg_batch *batch, const float *pts, int64_t N, tg_s
  * tg_batch_order), which keeps those accesses within each brick's range -
  * use it when the per-point work around the query (a loss, a sampler) can
  * run in that order too. Neither order needs scratch beyond the batch.
+ * Kernels: with at least 48 points per brick on average (96 when spatial
+ * gradients are asked for or given) one block per brick stages the brick's
+ * coefficient (or gradient) tile through shared memory; below that, or where
+ * a grid row of res x K x channels elements is not a whole number of 16-byte
+ * units, one thread per binned record gathers (or reduces into) its 8 corner
+ * blocks directly. The deterministic backward always takes the brick form.
+ * TG_BINNED_PATH=brick or =records in the environment (read at every call)
+ * forces one form, for measurements and tests.
  * Errors: TG_EINVAL (shape or order flag), TG_EDEVICE. */
 TG_API tg_status tg_query_binned(const tg_grid *grid, const tg_batch *batch,
                                  float *out, float *grad_x, int order_flags, tg_stream stream);
