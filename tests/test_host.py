@@ -74,6 +74,47 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     lib.tg_chamfer.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                ctypes.c_void_p]
     assert lib.tg_chamfer(None, 1, None, 1, None, None) == 1
+    lib.tg_measure_fp32_peak.argtypes = [ctypes.c_void_p]
+    assert lib.tg_measure_fp32_peak(None) == 1
+
+
+def test_fit_job_descriptions_are_checked_on_the_host(lib):
+    """The server and its submission queue are host objects: bad descriptions, unknown flags and jobs that can
+    never fit the budget are refused at submission, before anything touches the device."""
+    from paper_2402_14415_gb300.binding import FitDesc
+    s = ctypes.c_void_p()
+    lib.tg_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    lib.tg_server_destroy.argtypes = [ctypes.c_void_p]
+    lib.tg_fit_job.argtypes = [ctypes.c_void_p, ctypes.POINTER(FitDesc), ctypes.POINTER(ctypes.c_int64)]
+    assert lib.tg_server_create(0, 1, ctypes.byref(s)) == 1          # empty budget
+    assert lib.tg_server_create(1 << 30, 0, ctypes.byref(s)) == 1    # no running slot
+    assert lib.tg_server_create(1 << 30, 4, ctypes.byref(s)) == 0
+    sph = (ctypes.c_float * 4)(0.5, 0.5, 0.5, 0.3)
+    cdf = (ctypes.c_float * 1)(1.0)
+    jid = ctypes.c_int64(-1)
+
+    def desc(**kw):
+        d = FitDesc(res=64, order=2, dtype=0, seed=0, n_spheres=1, n_boxes=0,
+                    spheres=ctypes.cast(sph, ctypes.c_void_p), boxes=None, area_cdf=ctypes.cast(cdf, ctypes.c_void_p),
+                    points_per_step=1 << 16, eval_points=1 << 14, eval_every=10, max_steps=100, tol=0.0, lr=1e-2,
+                    lambda_eik=0.1, init_std=0.0, k_weight=0.0, lambda_tv=0.0, flags=0)
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    try:
+        assert lib.tg_fit_job(s, None, ctypes.byref(jid)) == 1
+        assert lib.tg_fit_job(s, ctypes.byref(desc(flags=4)), ctypes.byref(jid)) == 1     # unknown flag bit
+        assert lib.tg_fit_job(s, ctypes.byref(desc(dtype=7)), ctypes.byref(jid)) == 1
+        assert lib.tg_fit_job(s, ctypes.byref(desc(order=3)), ctypes.byref(jid)) == 1
+        assert lib.tg_fit_job(s, ctypes.byref(desc(res=1)), ctypes.byref(jid)) == 1
+        assert lib.tg_fit_job(s, ctypes.byref(desc(area_cdf=None)), ctypes.byref(jid)) == 1
+        assert lib.tg_fit_job(s, ctypes.byref(desc(n_spheres=0)), ctypes.byref(jid)) == 1  # no surface to sample
+        # 1024^3 order 2 in FP32: 10.7 G coefficients x 16 bytes, far over the 1 GiB budget
+        assert lib.tg_fit_job(s, ctypes.byref(desc(res=1024)), ctypes.byref(jid)) == 3
+        assert jid.value == -1                                                             # nothing was queued
+    finally:
+        assert lib.tg_server_destroy(s) == 0
 
 
 def test_product_path_has_no_oracle_reference():
