@@ -697,6 +697,25 @@ def test_marching_tets_empty_and_full():
     assert oracle.marching_tets(5, -np.ones(125)).shape[0] == 0
 
 
+def test_lattice_values_of_quadratic_grids():
+    """Two order-2 channels holding the Taylor data of two different quadratics (exchange layout
+    [vertex][channel][k]) reproduce them on a lattice that does not coincide with the grid's vertices: the
+    lattice is i (x) fastest and the channel argument selects the channel. A transposed lattice or the wrong
+    channel misses by O(1), since the quadratics differ along every axis."""
+    res, M = 6, 9
+    quads = [quadratic(3, 21), quadratic(3, 22)]
+    per = [taylor_data_of_poly(3, res, 2, *q).reshape(res ** 3, 1, -1) for q in quads]
+    coefs = np.concatenate(per, axis=1).reshape(-1)
+    a = np.arange(M, dtype=np.float64) / (M - 1)
+    lat = np.stack(np.meshgrid(a, a, a, indexing="ij")[::-1], -1).reshape(-1, 3)     # (x, y, z), x fastest
+    lat = lat.astype(np.float32).astype(np.float64)                                 # the FP32 query points
+    for ch, (p, _, _) in enumerate(quads):
+        vals = oracle.lattice_values(res, 2, 2, coefs, M, channel=ch)
+        np.testing.assert_allclose(vals, [p(v) for v in lat], atol=5e-6)
+    assert np.abs(oracle.lattice_values(res, 2, 2, coefs, M, channel=0)
+                  - np.array([quads[1][0](v) for v in lat])).max() > 0.1
+
+
 def test_sample_mesh_area_weighting_and_support():
     """Two triangles with areas 1 : 3: the samples split 1 : 3 and lie on their triangles; the mean of the
     samples on one triangle is its centroid."""
