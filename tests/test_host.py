@@ -125,3 +125,16 @@ def test_product_path_has_no_oracle_reference():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "tg_oracle" not in txt, f
+
+
+def test_binding_has_no_cpu_path(lib, monkeypatch):
+    """A host tensor is refused before any library call, and without the built library every call raises:
+    there is no CPU fallback behind the binding."""
+    import torch
+    from paper_2402_14415_gb300 import binding
+    with pytest.raises(ValueError, match="no CPU path"):
+        binding.tg_locate(3, 8, torch.rand((10, 3)))
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", os.path.join(ROOT, "paper_2402_14415_gb300", "_build", "absent.so"))
+    with pytest.raises(ImportError):
+        binding.tg_locate(3, 8, torch.rand((10, 3)))
